@@ -1,0 +1,392 @@
+"""Benchmark of the ACM-HD flux-reconstruction RHS on GB300.
+
+One step = one fused right-hand-side evaluation R = -div F(U) + S(U) (face
+trace kernel + fused kernel) of the 3-D Taylor-Green workload: p = 3 hexes
+(4^3 Gauss-Legendre points), 64^3 periodic mesh on [-pi, pi]^3, 13
+variables, FP32.  Metric: GDOF-RHS/s = n_elem * (p+1)^3 * 13 / t / 1e9.
+
+Printed as one JSON line (rank 0).  Besides `value` (device-resident
+inputs, CUDA events around exactly --steps steps) it carries:
+  e2e           the same metric through fr_rhs_host (pinned host buffers,
+                host->device and device->host copies inside the timed region)
+  roofline      the fused kernel's algorithmic bytes / its event-timed
+                duration, against the measured HBM copy bandwidth
+  unfused/fp64  the six-kernel Table-1 pipeline and the FP64 fused RHS,
+                timed the same way (context for the fused-vs-unfused ratio)
+  cpu_baseline  the FP64 oracle timed on this host's cores on a bounded
+                sample of the same workload
+  clocks        nvidia-smi samples taken during the timed region
+
+Multi-GPU (torchrun): every rank evaluates its own replica of the workload
+(the RHS of one mesh has a halo exchange that is not built), so the value
+is the DOF total over all ranks / the slowest rank's time ("weak").
+
+--impl reference times the FP64 oracle itself on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "hex_p3_64cube"
+METRIC = "GDOF-RHS/s"
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _source_digest():
+    h = hashlib.sha256()
+    for name in ("k_fused.cu", "fr_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_14027_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per fused launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "fused_hex_p3_64cube.json")
+    try:
+        with open(path) as f:
+            prof = json.load(f)
+        if prof.get("source_digest") == _source_digest():
+            return float(prof["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_baseline_subprocess(n_side, reps_s):
+    """Time the FP64 oracle RHS in a fresh single-threaded process on an
+    n_side^3 p = 3 sample of the workload; returns (gdof_per_s, seconds, desc)."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import fr
+from paper_2107_14027_gb300 import workloads as W
+cfg = W.WORKLOADS[{WORKLOAD!r}]
+n = ({n_side},) * 3
+h = (cfg['hi'][0] - cfg['lo'][0]) / cfg['n'][0]
+lo = (cfg['lo'][0],) * 3
+hi = (cfg['lo'][0] + h * {n_side},) * 3
+U = W.taylor_green(n, lo, hi, cfg['order'])
+mesh = fr.Mesh(n, lo, hi)
+prm = fr.Params(cfg['zeta'], cfg['nu'], cfg['t_r'])
+fr.rhs(U, mesh, cfg['order'], prm)
+t0 = time.perf_counter(); k = 0
+while True:
+    fr.rhs(U, mesh, cfg['order'], prm); k += 1
+    if time.perf_counter() - t0 > {reps_s}:
+        break
+dt = (time.perf_counter() - t0) / k
+print(json.dumps({{"t": dt, "reps": k, "dof": U.size}}))
+"""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        return None
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return res["dof"] / res["t"] / 1e9, res["t"], res["reps"]
+
+
+def run_reference(args):
+    rank, _, world = _rank_env()
+    if world > 1 and rank != 0:
+        return
+    # one oracle RHS on a 12^3-element p = 3 sample of the 64^3 workload per step
+    n_side = 12
+    code_steps = args.warmup + args.steps
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+from oracle import fr
+from paper_2107_14027_gb300 import workloads as W
+cfg = W.WORKLOADS[{WORKLOAD!r}]
+n = ({n_side},) * 3
+h = (cfg['hi'][0] - cfg['lo'][0]) / cfg['n'][0]
+lo = (cfg['lo'][0],) * 3
+hi = (cfg['lo'][0] + h * {n_side},) * 3
+U = W.taylor_green(n, lo, hi, cfg['order'])
+mesh = fr.Mesh(n, lo, hi)
+prm = fr.Params(cfg['zeta'], cfg['nu'], cfg['t_r'])
+ts = []
+for i in range({code_steps}):
+    t0 = time.perf_counter(); fr.rhs(U, mesh, cfg['order'], prm); ts.append(time.perf_counter() - t0)
+print(json.dumps({{"t": sum(ts[{args.warmup}:]), "dof": U.size}}))
+"""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    value = res["dof"] * args.steps / res["t"] / 1e9
+    sample = f"FP64 oracle RHS on a {n_side}^3-element p=3 piece of the 64^3 TGV workload per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * res["t"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "order": 3, "mesh": [64, 64, 64], "nvars": 13},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def _time_loop(fn, stream, steps, warmup, torch):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3  # seconds
+
+
+def run_gpu(args):
+    import torch
+    rank, local_rank, world = _rank_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2107_14027_gb300 import abi
+    from paper_2107_14027_gb300 import workloads as W
+    cfg = W.WORKLOADS[WORKLOAD]
+    n, order, nv = cfg["n"], cfg["order"], 13
+    m = order + 1
+    dof = int(np.prod(n)) * m ** 3 * nv
+
+    # CPU baseline first (fresh single-threaded process; no GPU state inherited)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline_subprocess(16, 10.0)
+
+    stream = torch.cuda.current_stream()
+    U32 = W.taylor_green(n, cfg["lo"], cfg["hi"], order, dtype=np.float32)
+    ctx = abi.fr_create(n, cfg["lo"], cfg["hi"], order, nv, cfg["zeta"], cfg["nu"], cfg["t_r"],
+                        abi.FR_F32, abi.FR_CORR_DG)
+    stride, ne, nbytes = abi.fr_layout(ctx)
+    Ud = abi.pack_state(ctx, U32, abi.FR_F32)
+    Rd = abi.new_state(ctx, abi.FR_F32)
+
+    def step():
+        abi.fr_rhs(ctx, Ud, Rd, stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up, then exactly --steps timed steps, clocks sampled meanwhile
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+        t_total = ev0.elapsed_time(ev1) / 1e3
+        if args.steps * (t_total / max(args.steps, 1)) < 1.0:
+            # keep the sampler alive for a few samples on very short runs
+            time.sleep(0.5)
+    t_max = t_total
+    if dist is not None:
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * dof * args.steps / t_max / 1e9
+
+    # per-kernel timing on the launching stream: the trace kernel alone
+    # (fr_trace) and the fused kernel alone (fr_rhs_volume, reading the
+    # traces of the same U)
+    K = max(args.steps, 10)
+    t_rhs_only = t_total / args.steps
+    trace_s = _time_loop(lambda: abi.fr_trace(ctx, Ud, stream), stream, K, 2, torch) / K
+    fused_s = _time_loop(lambda: abi.fr_rhs_volume(ctx, Ud, Rd, stream), stream, K, 2, torch) / K
+
+    # algorithmic bytes of one fused launch (FP32): read U and the 6 neighbour
+    # face traces of 7 slots, write R
+    alg_bytes = ne * (2 * nv * m ** 3 + 6 * 7 * m ** 2) * 4
+    hbm, peak_kind = _peaks()
+    achieved = alg_bytes / fused_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": _profiled_traffic(),
+                "kernel": "fused_kernel<3,4,float>", "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes}
+
+    # unfused pipeline and FP64 fused, same stream
+    t_unf = _time_loop(lambda: abi.fr_rhs_unfused(ctx, Ud, Rd, stream), stream, K, 2, torch) / K
+    abi.fr_destroy(ctx)
+    del Ud, Rd
+    torch.cuda.empty_cache()
+
+    U64 = U32.astype(np.float64)
+    ctx64 = abi.fr_create(n, cfg["lo"], cfg["hi"], order, nv, cfg["zeta"], cfg["nu"], cfg["t_r"],
+                          abi.FR_F64, abi.FR_CORR_DG)
+    Ud64 = abi.pack_state(ctx64, U64, abi.FR_F64)
+    Rd64 = abi.new_state(ctx64, abi.FR_F64)
+    t64 = _time_loop(lambda: abi.fr_rhs(ctx64, Ud64, Rd64, stream), stream, max(K // 2, 5), 2,
+                     torch) / max(K // 2, 5)
+    abi.fr_destroy(ctx64)
+    del Ud64, Rd64
+    torch.cuda.empty_cache()
+
+    # end to end through the public host-buffer call
+    ctx = abi.fr_create(n, cfg["lo"], cfg["hi"], order, nv, cfg["zeta"], cfg["nu"], cfg["t_r"],
+                        abi.FR_F32, abi.FR_CORR_DG)
+    stride, ne, nbytes = abi.fr_layout(ctx)
+    Uh = torch.empty((nbytes // 4,), dtype=torch.float32, pin_memory=True)
+    Uh.view(-1, stride)[:, :ne].copy_(torch.from_numpy(U32.reshape(-1, ne)))
+    Rh = torch.empty_like(Uh).pin_memory()
+    Ke = max(args.steps // 2, 3)
+    for _ in range(2):
+        abi.fr_rhs_host(ctx, Uh, Rh, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        abi.fr_rhs_host(ctx, Uh, Rh, stream)
+    barrier()
+    te = time.perf_counter() - t0
+    te_max = te
+    if dist is not None:
+        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te_max = float(tt.item())
+    e2e = {"value": world * dof * Ke / te_max / 1e9, "unit": "GDOF/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "call": "fr_rhs_host"}
+    abi.fr_destroy(ctx)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "order": order, "mesh": list(n), "nvars": nv,
+                       "elements": int(np.prod(n)), "dof": dof, "precision": "fp32",
+                       "l2": "inputs larger than L2 (state 872 MB, traces 440 MB)",
+                       "parallelism": f"replicas{world}"},
+            "e2e": e2e,
+            "roofline": roofline,
+            "kernels_ms": {"fused": 1e3 * fused_s, "trace": 1e3 * trace_s,
+                           "rhs": 1e3 * t_rhs_only},
+            "unfused": {"value": dof / t_unf / 1e9, "ms": 1e3 * t_unf,
+                        "fused_speedup": t_unf / t_rhs_only},
+            "fp64": {"value": dof / t64 / 1e9, "ms": 1e3 * t64},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+        }
+        if cpu is not None:
+            out["cpu_baseline"] = {"value": cpu[0], "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"FP64 oracle RHS, 16^3-element p=3 piece of the "
+                                             f"workload, {cpu[2]} reps, {cpu[1]:.2f} s each"}
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,154 @@
+/*
+ * acmhd_fr.h - C ABI of the GB300 (sm_103a) flux-reconstruction library for
+ * the artificial-compressibility Navier-Stokes equations with hyperbolised
+ * diffusion (ACM-HD).
+ *
+ * What is computed (paper: Trojak, Watson & Witherden, "Hyperbolic Diffusion
+ * in Flux Reconstruction: Optimisation through Kernel Fusion within
+ * Tensor-Product Elements"):
+ *   R = -div F(U) + S(U)
+ * for the ACM-HD system of Sec. 2.2 (Eq. acmhd_2d for d = 2, Eq. acmhd_nd for
+ * d = 3), discretised by flux reconstruction (Sec. 2.1, FR divergence
+ * equation) on a periodic, uniform, axis-aligned mesh of affine quadrilateral
+ * or hexahedral elements with (p+1)^d Gauss-Legendre solution points, using
+ * the six stages of Table fr_adv.  Common interface flux: Rusanov on the
+ * hyperbolic (P, V) equations and the mean flux on the auxiliary equations
+ * (Sec. 5).
+ *
+ * Variables (n_v = 1 + d + d^2): P, V = (u, v[, w]), then d(V_i)/dx_b at
+ * index 1 + d + i*d + b.  3-D: P,u,v,w,qx,qy,qz,rx,ry,rz,sx,sy,sz.
+ *
+ * State layout ("SoA, elements fastest"): a state is one device buffer of
+ * n_v * (p+1)^d * elem_stride values of the context's precision (float or
+ * double), value (v, pt, e) at offset (v * (p+1)^d + pt) * elem_stride + e,
+ * with pt = i + m j + m^2 k (i along x, m = p + 1) and
+ * e = ex + nx (ey + ny ez).  elem_stride >= n_elem is a multiple of 32
+ * (fr_layout reports it); padding entries are read but never influence
+ * entries e < n_elem, and are written with unspecified values.  Device
+ * pointers must be 16-byte aligned.
+ *
+ * Ownership: the caller owns every state buffer it passes.  The context owns
+ * its operator constants, face-trace scratch and time-stepping registers,
+ * which fr_destroy releases.  A context is bound to the device that was
+ * current when fr_create ran; calls must be made with that device current.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Unless
+ * stated otherwise, calls only enqueue work and do not synchronise the host.
+ * Calls on one context must not overlap on different streams (the context's
+ * scratch is shared).
+ *
+ * Errors: every call returns FR_OK (0) or a negative code; nothing throws
+ * across the ABI.  FR_ECUDA carries the last CUDA error text, readable with
+ * fr_last_error(); fr_strerror() maps a code to a fixed string.
+ */
+#ifndef ACMHD_FR_H
+#define ACMHD_FR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FR_ABI_VERSION 1
+
+typedef struct fr_ctx fr_ctx;
+
+/* Periodic, uniform, axis-aligned mesh: n[a] elements on [lo[a], hi[a]]
+ * along direction a (a < dim).  Entries a >= dim are ignored. */
+typedef struct fr_mesh {
+    int dim;          /* 2 or 3 */
+    int n[3];         /* elements per direction, each >= 1 */
+    double lo[3];
+    double hi[3];     /* hi[a] > lo[a] */
+} fr_mesh;
+
+enum {
+    FR_OK = 0,
+    FR_EINVAL = -1,      /* bad argument: mesh, order, nvars, parameters, pointer */
+    FR_ECUDA = -2,       /* a CUDA runtime call or kernel launch failed */
+    FR_ENOCONV = -3,     /* pseudo-time iteration hit max_iter above tolerance */
+    FR_ENONFINITE = -4,  /* a residual norm was NaN or Inf */
+    FR_ENOMEM = -5,      /* device or host allocation failed */
+    FR_ETIMEOUT = -6     /* a bounded in-kernel wait gave up (see fr_check) */
+};
+
+enum { FR_F32 = 32, FR_F64 = 64 };           /* arithmetic precision */
+enum { FR_CORR_DG = 0, FR_CORR_G2 = 1 };     /* correction function (Sec. 2.1) */
+
+/* Create a context.
+ *   order       p, 1..6 (m = p + 1 solution points per direction)
+ *   nvars       must equal 1 + dim + dim^2 (7 in 2-D, 13 in 3-D)
+ *   zeta        artificial compressibility zeta > 0 (Sec. 2.2)
+ *   nu          kinematic viscosity nu >= 0
+ *   t_r         relaxation time T_r > 0 of the auxiliary equations
+ *   precision   FR_F32 or FR_F64
+ *   correction  FR_CORR_DG (right Radau, h_l = R_{R,p+1}) or FR_CORR_G2 (Huynh)
+ * Allocates the context's device scratch on the current device.
+ * Returns FR_EINVAL for bad arguments, FR_ENOMEM/FR_ECUDA on allocation
+ * failure; *out is set only on success. */
+int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
+              double t_r, int precision, int correction, fr_ctx** out);
+
+/* Release a context and its device memory (NULL is a no-op).  Synchronises
+ * the device before freeing. */
+void fr_destroy(fr_ctx* ctx);
+
+/* Layout of a state: elements per row (padded), number of real elements,
+ * and the byte size of one state buffer.  Any output pointer may be NULL. */
+int fr_layout(const fr_ctx* ctx, size_t* elem_stride, size_t* n_elem,
+              size_t* bytes_per_state);
+
+/* Fused right-hand side R = -div F(U) + S(U) (Table fr_adv stages 1-6).
+ * Two kernels: a face-trace kernel (stage 1, only the 1 + 2d variables the
+ * normal flux needs) and one fused kernel that evaluates the flux (stage 2),
+ * the partially corrected divergence (3), the Rusanov/mean common flux (4),
+ * the correction (5) and negation plus source (6) per element.
+ * U, R: device state buffers (must not alias).  Uses the context's trace
+ * scratch.  Asynchronous on `stream`. */
+int fr_rhs(fr_ctx* ctx, const void* U, void* R, void* stream);
+
+/* The two halves of fr_rhs, for callers that time or schedule them apart.
+ * fr_trace: stage 1 only - interpolates U to the faces of every element
+ * (the 1 + 2d slots each face needs) into the context's trace scratch.
+ * fr_rhs_volume: stages 2-6 - the fused kernel, reading U and the traces
+ * that the last fr_trace on this context wrote.  The caller must pass the
+ * same U to both and keep it unchanged in between; fr_rhs(U, R) is
+ * fr_trace(U) followed by fr_rhs_volume(U, R). */
+int fr_trace(fr_ctx* ctx, const void* U, void* stream);
+int fr_rhs_volume(fr_ctx* ctx, const void* U, void* R, void* stream);
+
+/* The same R computed by six separate stage kernels with HBM intermediates,
+ * exactly as laid out in Table fr_adv (dense flux array F_s[d n_v n_s],
+ * traces of all n_v variables).  The unfused baseline.  Allocates its
+ * intermediates on first use (FR_ENOMEM on failure). */
+int fr_rhs_unfused(fr_ctx* ctx, const void* U, void* R, void* stream);
+
+/* fr_rhs on HOST buffers: copies U (bytes_per_state bytes, host memory,
+ * preferably pinned) to context-owned device staging, evaluates the fused
+ * RHS and copies R back to host memory.  Synchronises `stream` before
+ * returning.  Allocates the staging on first use. */
+int fr_rhs_host(fr_ctx* ctx, const void* U_host, void* R_host, void* stream);
+
+/* One classical RK4 step in pseudo time of dU/dtau = R(U) (Sec. 5, read as
+ * RK4 with a fixed step): U <- U + dtau/6 (k1 + 2 k2 + 2 k3 + k4), in place.
+ * Uses the context's RK registers.  Asynchronous. */
+int fr_rk_step(fr_ctx* ctx, void* U, double dtau, void* stream);
+
+/* Reads the context's device error word after synchronising `stream`;
+ * returns FR_ETIMEOUT if a bounded in-kernel wait gave up since the last
+ * call (and clears it), else FR_OK or FR_ECUDA. */
+int fr_check(fr_ctx* ctx, void* stream);
+
+/* Static text for a status code. */
+const char* fr_strerror(int status);
+
+/* Text of the last CUDA error seen by this library in the calling thread
+ * (empty if none). */
+const char* fr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACMHD_FR_H */

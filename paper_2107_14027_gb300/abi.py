@@ -1,0 +1,203 @@
+"""Thin Python binding of the C ABI in include/acmhd_fr.h (ctypes).
+
+The functions carry the same names as the C entry points and only marshal
+arguments: torch tensors become device pointers, the current torch stream
+becomes the cudaStream_t, non-zero status codes become FrError.  Every
+step of the computation runs in the CUDA library; if the library is
+missing, loading fails loudly (there is no fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libacmhd_fr.so")
+
+FR_OK, FR_EINVAL, FR_ECUDA, FR_ENOCONV, FR_ENONFINITE, FR_ENOMEM, FR_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+FR_F32, FR_F64 = 32, 64
+FR_CORR_DG, FR_CORR_G2 = 0, 1
+
+EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_trace", "fr_rhs_volume",
+           "fr_rhs_unfused", "fr_rhs_host",
+           "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error"]
+
+
+class fr_mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class FrError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_lib().fr_strerror(status).decode()} ({status})"
+                         + (f" [{_lib().fr_last_error().decode()}]" if status == FR_ECUDA else ""))
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run python -m paper_2107_14027_gb300.build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, sz, dbl, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_double, ctypes.c_int
+        lib.fr_create.argtypes = [ctypes.POINTER(fr_mesh), i32, i32, dbl, dbl, dbl, i32, i32,
+                                  ctypes.POINTER(vp)]
+        lib.fr_destroy.argtypes = [vp]
+        lib.fr_destroy.restype = None
+        lib.fr_layout.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(sz)]
+        for name in ("fr_rhs", "fr_rhs_volume", "fr_rhs_unfused", "fr_rhs_host"):
+            getattr(lib, name).argtypes = [vp, vp, vp, vp]
+        lib.fr_trace.argtypes = [vp, vp, vp]
+        lib.fr_rk_step.argtypes = [vp, vp, dbl, vp]
+        lib.fr_check.argtypes = [vp, vp]
+        lib.fr_strerror.argtypes = [i32]
+        lib.fr_strerror.restype = ctypes.c_char_p
+        lib.fr_last_error.argtypes = []
+        lib.fr_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("fr_destroy", "fr_strerror", "fr_last_error"):
+                getattr(lib, name).restype = i32
+        _LIB = lib
+    return _LIB
+
+
+def _check(status, where):
+    if status != FR_OK:
+        raise FrError(status, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_mesh(n, lo, hi):
+    d = len(n)
+    m = fr_mesh()
+    m.dim = d
+    for a in range(3):
+        m.n[a] = int(n[a]) if a < d else 1
+        m.lo[a] = float(lo[a]) if a < d else 0.0
+        m.hi[a] = float(hi[a]) if a < d else 1.0
+    return m
+
+
+def fr_create(n, lo, hi, order, nvars, zeta, nu, t_r, precision=FR_F32, correction=FR_CORR_DG):
+    """Returns an opaque context handle (int)."""
+    mesh = make_mesh(n, lo, hi)
+    out = ctypes.c_void_p()
+    _check(_lib().fr_create(ctypes.byref(mesh), int(order), int(nvars), float(zeta), float(nu),
+                            float(t_r), int(precision), int(correction), ctypes.byref(out)),
+           "fr_create")
+    return out.value
+
+
+def fr_create_raw(mesh, order, nvars, zeta, nu, t_r, precision, correction):
+    """fr_create on a prepared fr_mesh (or None); returns (status, handle)."""
+    out = ctypes.c_void_p()
+    st = _lib().fr_create(ctypes.byref(mesh) if mesh is not None else None, int(order), int(nvars),
+                          float(zeta), float(nu), float(t_r), int(precision), int(correction),
+                          ctypes.byref(out))
+    return st, out.value
+
+
+def fr_destroy(ctx):
+    _lib().fr_destroy(ctypes.c_void_p(ctx))
+
+
+def fr_layout(ctx):
+    """(elem_stride, n_elem, bytes_per_state)"""
+    s, n, b = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib().fr_layout(ctypes.c_void_p(ctx), ctypes.byref(s), ctypes.byref(n), ctypes.byref(b)),
+           "fr_layout")
+    return s.value, n.value, b.value
+
+
+def fr_rhs(ctx, U, R, stream=None):
+    _check(_lib().fr_rhs(ctypes.c_void_p(ctx), _ptr(U), _ptr(R), _stream(stream)), "fr_rhs")
+
+
+def fr_trace(ctx, U, stream=None):
+    _check(_lib().fr_trace(ctypes.c_void_p(ctx), _ptr(U), _stream(stream)), "fr_trace")
+
+
+def fr_rhs_volume(ctx, U, R, stream=None):
+    _check(_lib().fr_rhs_volume(ctypes.c_void_p(ctx), _ptr(U), _ptr(R), _stream(stream)),
+           "fr_rhs_volume")
+
+
+def fr_rhs_unfused(ctx, U, R, stream=None):
+    _check(_lib().fr_rhs_unfused(ctypes.c_void_p(ctx), _ptr(U), _ptr(R), _stream(stream)),
+           "fr_rhs_unfused")
+
+
+def fr_rhs_host(ctx, U_host, R_host, stream=None):
+    """U_host, R_host: CPU torch tensors (pinned for speed) or numpy arrays."""
+    def hp(x):
+        if isinstance(x, np.ndarray):
+            return ctypes.c_void_p(x.ctypes.data)
+        return ctypes.c_void_p(x.data_ptr())
+    _check(_lib().fr_rhs_host(ctypes.c_void_p(ctx), hp(U_host), hp(R_host), _stream(stream)),
+           "fr_rhs_host")
+
+
+def fr_rk_step(ctx, U, dtau, stream=None):
+    _check(_lib().fr_rk_step(ctypes.c_void_p(ctx), _ptr(U), float(dtau), _stream(stream)),
+           "fr_rk_step")
+
+
+def fr_check(ctx, stream=None):
+    _check(_lib().fr_check(ctypes.c_void_p(ctx), _stream(stream)), "fr_check")
+
+
+def fr_strerror(status):
+    return _lib().fr_strerror(int(status)).decode()
+
+
+# ---------------------------------------------------------------------------
+# layout marshalling (padding of the element axis only)
+# ---------------------------------------------------------------------------
+
+def torch_dtype(precision):
+    import torch
+    return torch.float32 if precision == FR_F32 else torch.float64
+
+
+def new_state(ctx, precision, device="cuda", fill=0.0):
+    import torch
+    stride, ne, nbytes = fr_layout(ctx)
+    esz = 4 if precision == FR_F32 else 8
+    rows = nbytes // (esz * stride)
+    return torch.full((rows, stride), fill, dtype=torch_dtype(precision), device=device)
+
+
+def pack_state(ctx, U, precision, device="cuda"):
+    """[nv, npts, ne] numpy -> padded [nv*npts, stride] torch tensor on device."""
+    import torch
+    stride, ne, _ = fr_layout(ctx)
+    nv, npts, ne_in = U.shape
+    assert ne_in == ne
+    host = np.zeros((nv * npts, stride), dtype=np.float32 if precision == FR_F32 else np.float64)
+    host[:, :ne] = U.reshape(nv * npts, ne)
+    return torch.from_numpy(host).to(device)
+
+
+def unpack_state(ctx, T, nv):
+    """padded device tensor -> [nv, npts, ne] numpy FP64."""
+    stride, ne, _ = fr_layout(ctx)
+    A = T.detach().cpu().numpy().astype(np.float64)
+    return A[:, :ne].reshape(nv, -1, ne)

@@ -1,0 +1,269 @@
+// C ABI of the ACM-HD flux-reconstruction library (declared in acmhd_fr.h):
+// argument checking, context and scratch ownership, and the sequencing of
+// kernel launches.  All arithmetic of the method runs in the k_*.cu kernels.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "fr_internal.h"
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+void set_cuda_error(cudaError_t e, const char* where) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
+int cuda_status(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return FR_OK;
+  set_cuda_error(e, where);
+  return (e == cudaErrorMemoryAllocation) ? FR_ENOMEM : FR_ECUDA;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <typename T>
+void fill_const(const fr_ctx* c, acmhd::FrConst<T>* k) {
+  std::memset(k, 0, sizeof(*k));
+  const acmhd::Ops1D& o = c->ops;
+  for (int a = 0; a < c->dim; ++a) {
+    const double h = (c->mesh.hi[a] - c->mesh.lo[a]) / c->mesh.n[a];
+    const double J = 2.0 / h;
+    k->J[a] = static_cast<T>(J);
+    for (int i = 0; i < o.m; ++i) {
+      for (int q = 0; q < o.m; ++q) k->A[a][i][q] = static_cast<T>(-J * o.Dt[i][q]);
+      k->bl[a][i] = static_cast<T>(-J * o.dhl[i]);
+      k->br[a][i] = static_cast<T>(-J * o.dhr[i]);
+    }
+  }
+  for (int i = 0; i < o.m; ++i) {
+    for (int q = 0; q < o.m; ++q) k->Dt[i][q] = static_cast<T>(o.Dt[i][q]);
+    k->dhl[i] = static_cast<T>(o.dhl[i]);
+    k->dhr[i] = static_cast<T>(o.dhr[i]);
+    k->lm[i] = static_cast<T>(o.lm[i]);
+    k->lp[i] = static_cast<T>(o.lp[i]);
+  }
+  k->zeta = static_cast<T>(c->zeta);
+  k->nu = static_cast<T>(c->nu);
+  k->inv_t = static_cast<T>(1.0 / c->t_r);
+  k->n[0] = c->mesh.n[0];
+  k->n[1] = c->mesh.n[1];
+  k->n[2] = c->dim == 3 ? c->mesh.n[2] : 1;
+  k->ne = c->ne;
+  k->stride = static_cast<int>(c->stride);
+}
+
+int alloc_zeroed(void** p, size_t bytes, const char* what) {
+  if (*p) return FR_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_status(e, what);
+  }
+  e = cudaMemset(*p, 0, bytes);
+  return cuda_status(e, what);
+}
+
+int ensure_rk(fr_ctx* c) {
+  int st;
+  if ((st = alloc_zeroed(&c->rk_stage, c->bytes_state, "rk registers")) != FR_OK) return st;
+  if ((st = alloc_zeroed(&c->rk_acc, c->bytes_state, "rk registers")) != FR_OK) return st;
+  return alloc_zeroed(&c->rk_k, c->bytes_state, "rk registers");
+}
+
+int ensure_unfused(fr_ctx* c) {
+  const size_t nl = c->npts / c->m;
+  const size_t row = c->stride * c->elem_bytes;
+  int st;
+  if ((st = alloc_zeroed(&c->unf_uf, 2 * c->dim * c->nv * nl * row, "unfused traces")) != FR_OK)
+    return st;
+  if ((st = alloc_zeroed(&c->unf_f, (size_t)c->dim * c->bytes_state, "unfused flux")) != FR_OK)
+    return st;
+  if ((st = alloc_zeroed(&c->unf_div, c->bytes_state, "unfused divergence")) != FR_OK) return st;
+  return alloc_zeroed(&c->unf_fi, 2 * c->dim * c->nv * nl * row, "unfused common flux");
+}
+
+bool bad_state_ptr(const void* p) { return p == nullptr || !aligned16(p); }
+
+}  // namespace
+
+extern "C" {
+
+int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu, double t_r,
+              int precision, int correction, fr_ctx** out) {
+  g_last_error[0] = '\0';
+  if (!mesh || !out) return FR_EINVAL;
+  const int d = mesh->dim;
+  if (d != 2 && d != 3) return FR_EINVAL;
+  if (order < 1 || order > acmhd::kMaxM - 1) return FR_EINVAL;
+  if (nvars != 1 + d + d * d) return FR_EINVAL;
+  if (precision != FR_F32 && precision != FR_F64) return FR_EINVAL;
+  if (correction != FR_CORR_DG && correction != FR_CORR_G2) return FR_EINVAL;
+  if (!(zeta > 0.0) || !(nu >= 0.0) || !(t_r > 0.0) || !std::isfinite(zeta) ||
+      !std::isfinite(nu) || !std::isfinite(t_r))
+    return FR_EINVAL;
+  long long ne = 1;
+  for (int a = 0; a < d; ++a) {
+    if (mesh->n[a] < 1) return FR_EINVAL;
+    if (!(mesh->hi[a] > mesh->lo[a]) || !std::isfinite(mesh->hi[a] - mesh->lo[a]))
+      return FR_EINVAL;
+    ne *= mesh->n[a];
+  }
+  if (ne > (1LL << 30)) return FR_EINVAL;
+
+  fr_ctx* c = new (std::nothrow) fr_ctx;
+  if (!c) return FR_ENOMEM;
+  std::memset(c, 0, sizeof(*c));
+  c->dim = d;
+  c->order = order;
+  c->m = order + 1;
+  c->nv = nvars;
+  c->precision = precision;
+  c->correction = correction;
+  c->mesh = *mesh;
+  c->zeta = zeta;
+  c->nu = nu;
+  c->t_r = t_r;
+  c->ne = static_cast<int>(ne);
+  c->stride = (static_cast<size_t>(ne) + 31) / 32 * 32;
+  c->npts = 1;
+  for (int a = 0; a < d; ++a) c->npts *= c->m;
+  c->elem_bytes = precision == FR_F32 ? 4 : 8;
+  c->bytes_state = (size_t)c->nv * c->npts * c->stride * c->elem_bytes;
+  if (c->stride > 0x7fffffff) {
+    delete c;
+    return FR_EINVAL;
+  }
+  if (!acmhd::build_ops1d(order, correction, &c->ops)) {
+    delete c;
+    return FR_EINVAL;
+  }
+  fill_const<float>(c, &c->cf);
+  fill_const<double>(c, &c->cd);
+
+  int st = cuda_status(cudaGetDevice(&c->device), "cudaGetDevice");
+  if (st == FR_OK) {
+    const size_t nl = c->npts / c->m;
+    c->trace_bytes = (size_t)(2 * d) * (1 + 2 * d) * nl * c->stride * c->elem_bytes;
+    st = alloc_zeroed(&c->trace, c->trace_bytes, "trace scratch");
+  }
+  if (st == FR_OK) st = alloc_zeroed(reinterpret_cast<void**>(&c->err), sizeof(int), "error word");
+  if (st != FR_OK) {
+    fr_destroy(c);
+    return st;
+  }
+  *out = c;
+  return FR_OK;
+}
+
+void fr_destroy(fr_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  void* bufs[] = {c->trace, c->rk_stage, c->rk_acc, c->rk_k, c->unf_uf, c->unf_f,
+                  c->unf_div, c->unf_fi, c->host_u, c->host_r, c->err};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+int fr_layout(const fr_ctx* c, size_t* elem_stride, size_t* n_elem, size_t* bytes_per_state) {
+  if (!c) return FR_EINVAL;
+  if (elem_stride) *elem_stride = c->stride;
+  if (n_elem) *n_elem = static_cast<size_t>(c->ne);
+  if (bytes_per_state) *bytes_per_state = c->bytes_state;
+  return FR_OK;
+}
+
+int fr_rhs(fr_ctx* c, const void* U, void* R, void* stream) {
+  if (!c || bad_state_ptr(U) || bad_state_ptr(R) || U == R) return FR_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = cuda_status(acmhd::launch_trace(c, U, c->trace, s), "trace kernel");
+  if (st != FR_OK) return st;
+  return cuda_status(acmhd::launch_fused(c, U, c->trace, R, s), "fused kernel");
+}
+
+int fr_trace(fr_ctx* c, const void* U, void* stream) {
+  if (!c || bad_state_ptr(U)) return FR_EINVAL;
+  return cuda_status(acmhd::launch_trace(c, U, c->trace, static_cast<cudaStream_t>(stream)),
+                     "trace kernel");
+}
+
+int fr_rhs_volume(fr_ctx* c, const void* U, void* R, void* stream) {
+  if (!c || bad_state_ptr(U) || bad_state_ptr(R) || U == R) return FR_EINVAL;
+  return cuda_status(acmhd::launch_fused(c, U, c->trace, R, static_cast<cudaStream_t>(stream)),
+                     "fused kernel");
+}
+
+int fr_rhs_unfused(fr_ctx* c, const void* U, void* R, void* stream) {
+  if (!c || bad_state_ptr(U) || bad_state_ptr(R) || U == R) return FR_EINVAL;
+  int st = ensure_unfused(c);
+  if (st != FR_OK) return st;
+  return cuda_status(acmhd::launch_unfused(c, U, R, static_cast<cudaStream_t>(stream)),
+                     "unfused kernels");
+}
+
+int fr_rhs_host(fr_ctx* c, const void* U_host, void* R_host, void* stream) {
+  if (!c || !U_host || !R_host) return FR_EINVAL;
+  int st;
+  if ((st = alloc_zeroed(&c->host_u, c->bytes_state, "host staging")) != FR_OK) return st;
+  if ((st = alloc_zeroed(&c->host_r, c->bytes_state, "host staging")) != FR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = cuda_status(cudaMemcpyAsync(c->host_u, U_host, c->bytes_state, cudaMemcpyHostToDevice, s),
+                   "copy to device");
+  if (st == FR_OK) st = fr_rhs(c, c->host_u, c->host_r, stream);
+  if (st == FR_OK)
+    st = cuda_status(
+        cudaMemcpyAsync(R_host, c->host_r, c->bytes_state, cudaMemcpyDeviceToHost, s),
+        "copy to host");
+  if (st == FR_OK) st = cuda_status(cudaStreamSynchronize(s), "stream synchronize");
+  return st;
+}
+
+int fr_rk_step(fr_ctx* c, void* U, double dtau, void* stream) {
+  if (!c || bad_state_ptr(U) || !std::isfinite(dtau)) return FR_EINVAL;
+  int st = ensure_rk(c);
+  if (st != FR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int stage = 0; stage < 4; ++stage) {
+    const void* in = stage == 0 ? U : c->rk_stage;
+    if ((st = fr_rhs(c, in, c->rk_k, stream)) != FR_OK) return st;
+    st = cuda_status(acmhd::launch_rk_stage(c, stage, dtau, U, s), "rk update");
+    if (st != FR_OK) return st;
+  }
+  return FR_OK;
+}
+
+int fr_check(fr_ctx* c, void* stream) {
+  if (!c) return FR_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int flag = 0;
+  int st = cuda_status(cudaMemcpyAsync(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost, s),
+                       "read error word");
+  if (st == FR_OK) st = cuda_status(cudaStreamSynchronize(s), "stream synchronize");
+  if (st != FR_OK) return st;
+  if (flag != 0) {
+    st = cuda_status(cudaMemsetAsync(c->err, 0, sizeof(int), s), "clear error word");
+    return st == FR_OK ? FR_ETIMEOUT : st;
+  }
+  return FR_OK;
+}
+
+const char* fr_strerror(int status) {
+  switch (status) {
+    case FR_OK: return "success";
+    case FR_EINVAL: return "invalid argument";
+    case FR_ECUDA: return "CUDA error";
+    case FR_ENOCONV: return "pseudo-time iteration did not converge";
+    case FR_ENONFINITE: return "non-finite residual";
+    case FR_ENOMEM: return "out of memory";
+    case FR_ETIMEOUT: return "bounded in-kernel wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* fr_last_error(void) { return g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Device-side building blocks shared by the trace, fused and unfused kernels.
+//
+// Face vectors use "slots": for a face with normal along axis a the normal
+// flux F_a of ACM-HD (Sec. 2.2, Eq. acmhd_nd) is non-zero in exactly 1 + 2d
+// equations (Sec. 3, sparsity equation): slot 0 = P, slots 1..d = V_i, slots
+// d+1..2d = the auxiliary equation d(V_i)/dx_a.  Only these slots of the
+// face traces are ever needed.
+//
+// Functions whose results must agree bit for bit between the two elements
+// that share a face (face traces, the common flux) use explicit
+// round-to-nearest intrinsics, so the compiler cannot contract or reorder
+// them differently at different call sites.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fr_internal.h"
+
+namespace acmhd {
+
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rn_sqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double rn_sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double vabs(double a) { return fabs(a); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+
+// variable index of d(V_i)/dx_b
+template <int D>
+__host__ __device__ constexpr int aux_var(int i, int b) {
+  return 1 + D + i * D + b;
+}
+
+// variable held in slot s of a face with normal axis a
+template <int D>
+__host__ __device__ constexpr int slot_var(int s, int a) {
+  return s <= D ? s : aux_var<D>(s - D - 1, a);
+}
+
+template <int M>
+__host__ __device__ constexpr int ipow(int e) {
+  return e == 0 ? 1 : M * ipow<M>(e - 1);
+}
+
+// point index of the t-th point of line l along axis a (pt = i + m j + m^2 k;
+// the line index enumerates the other coordinates, lower axis fastest)
+template <int D, int M>
+__host__ __device__ __forceinline__ int line_pt(int a, int l, int t) {
+  const int ma = (a == 0) ? 1 : (a == 1 ? M : M * M);
+  return (l % ma) + ma * t + ma * M * (l / ma);
+}
+
+// Interpolation of a line to one end: sum_k ell_k x_k, fixed order, explicit FMA.
+template <int M, typename T>
+__device__ __forceinline__ T trace_dot(const T (&x)[M], const T* ell) {
+  T acc = rn_mul(x[0], ell[0]);
+#pragma unroll
+  for (int k = 1; k < M; ++k) acc = rn_fma(x[k], ell[k], acc);
+  return acc;
+}
+
+// Normal flux F_a in slot order from the slot values u[0..2D].
+template <int D, typename T>
+__device__ __forceinline__ void slot_flux(const T (&u)[1 + 2 * D], int a, T zeta, T nu,
+                                          T inv_t, T (&f)[1 + 2 * D]) {
+  const T va = u[1 + a];
+  f[0] = rn_mul(zeta, va);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    // V_i V_a + P delta_ia - nu d(V_i)/dx_a
+    T t = rn_mul(nu, u[1 + D + i]);
+    t = (i == a) ? rn_sub(u[0], t) : -t;
+    f[1 + i] = rn_fma(u[1 + i], va, t);
+    f[1 + D + i] = -rn_mul(u[1 + i], inv_t);
+  }
+}
+
+// Common interface flux on a face with normal +e_a, uL on the low side:
+// mean flux plus Rusanov dissipation (s/2)(uR - uL) on P and V, where
+// s = max(|V_a| + sqrt(V_a^2 + zeta)) over both sides (Sec. 5).
+template <int D, typename T>
+__device__ __forceinline__ void common_flux(const T (&uL)[1 + 2 * D], const T (&uR)[1 + 2 * D],
+                                            int a, T zeta, T nu, T inv_t,
+                                            T (&fi)[1 + 2 * D]) {
+  T fL[1 + 2 * D], fR[1 + 2 * D];
+  slot_flux<D>(uL, a, zeta, nu, inv_t, fL);
+  slot_flux<D>(uR, a, zeta, nu, inv_t, fR);
+  const T vl = uL[1 + a], vr = uR[1 + a];
+  const T sl = rn_add(vabs(vl), rn_sqrt(rn_fma(vl, vl, zeta)));
+  const T sr = rn_add(vabs(vr), rn_sqrt(rn_fma(vr, vr, zeta)));
+  const T hs = rn_mul(T(0.5), vmax(sl, sr));
+#pragma unroll
+  for (int s = 0; s < 1 + 2 * D; ++s) {
+    const T mean = rn_mul(T(0.5), rn_add(fL[s], fR[s]));
+    fi[s] = (s <= D) ? rn_fma(-hs, rn_sub(uR[s], uL[s]), mean) : mean;
+  }
+}
+
+// Element coordinates and neighbours on the periodic mesh.
+template <int D>
+__device__ __forceinline__ void neighbours(int e, const int* n, int (&nb)[3][2]) {
+  const int ex = e % n[0];
+  const int r = e / n[0];
+  const int ey = (D == 3) ? r % n[1] : r;
+  const int ez = (D == 3) ? r / n[1] : 0;
+  const int sy = n[0], sz = n[0] * n[1];
+  nb[0][0] = e + ((ex == 0) ? n[0] - 1 : -1);
+  nb[0][1] = e + ((ex == n[0] - 1) ? 1 - n[0] : 1);
+  nb[1][0] = e + ((ey == 0) ? (n[1] - 1) * sy : -sy);
+  nb[1][1] = e + ((ey == n[1] - 1) ? (1 - n[1]) * sy : sy);
+  if (D == 3) {
+    nb[2][0] = e + ((ez == 0) ? (n[2] - 1) * sz : -sz);
+    nb[2][1] = e + ((ez == n[2] - 1) ? (1 - n[2]) * sz : sz);
+  } else {
+    nb[2][0] = nb[2][1] = e;
+  }
+}
+
+}  // namespace acmhd
+
+// Dispatch a runtime (dim, m) pair to a template call FN<D, M>(args...).
+#define ACMHD_DISPATCH_DM(dim, m, CALL)                        \
+  do {                                                         \
+    switch ((dim) * 10 + (m)) {                                \
+      case 22: { constexpr int D_ = 2, M_ = 2; CALL; } break;  \
+      case 23: { constexpr int D_ = 2, M_ = 3; CALL; } break;  \
+      case 24: { constexpr int D_ = 2, M_ = 4; CALL; } break;  \
+      case 25: { constexpr int D_ = 2, M_ = 5; CALL; } break;  \
+      case 26: { constexpr int D_ = 2, M_ = 6; CALL; } break;  \
+      case 27: { constexpr int D_ = 2, M_ = 7; CALL; } break;  \
+      case 32: { constexpr int D_ = 3, M_ = 2; CALL; } break;  \
+      case 33: { constexpr int D_ = 3, M_ = 3; CALL; } break;  \
+      case 34: { constexpr int D_ = 3, M_ = 4; CALL; } break;  \
+      case 35: { constexpr int D_ = 3, M_ = 5; CALL; } break;  \
+      case 36: { constexpr int D_ = 3, M_ = 6; CALL; } break;  \
+      case 37: { constexpr int D_ = 3, M_ = 7; CALL; } break;  \
+      default: return cudaErrorInvalidValue;                   \
+    }                                                          \
+  } while (0)

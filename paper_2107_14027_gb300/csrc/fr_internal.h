@@ -1,0 +1,92 @@
+// Internal declarations of the ACM-HD flux-reconstruction library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "acmhd_fr.h"
+
+namespace acmhd {
+
+constexpr int kMaxM = 7;  // p <= 6
+
+// 1-D operators of FR for m = p + 1 Gauss-Legendre solution points, FP64.
+// Sec. 2.1 (FR divergence equation): l_k Lagrange basis, h_l / h_r the left
+// and right correction functions with h_l(-1) = h_r(1) = 1, h_l(1) = h_r(-1) = 0.
+struct Ops1D {
+  int m;
+  double xi[kMaxM], w[kMaxM];
+  double D[kMaxM][kMaxM];   // D[i][k] = l_k'(xi_i)
+  double lm[kMaxM];         // l_k(-1)
+  double lp[kMaxM];         // l_k(+1)
+  double dhl[kMaxM];        // h_l'(xi_i)
+  double dhr[kMaxM];        // h_r'(xi_i)
+  double Dt[kMaxM][kMaxM];  // partially corrected divergence operator
+                            // D - h_l' l(-1)^T - h_r' l(+1)^T (Table fr_adv, stage 3)
+};
+
+// Builds the operators; correction is FR_CORR_DG or FR_CORR_G2.
+bool build_ops1d(int order, int correction, Ops1D* out);
+
+// Everything a kernel needs, passed by value (lands in the constant bank).
+template <typename T>
+struct FrConst {
+  // fused kernel: per-axis operators pre-scaled by -J_a (J_a = 2 / h_a), so
+  // that R gets  sum_k A[a][i][k] F_k + bl[a][i] F^I_l + br[a][i] F^I_r
+  T A[3][kMaxM][kMaxM];
+  T bl[3][kMaxM];
+  T br[3][kMaxM];
+  // unscaled operators (unfused stage kernels)
+  T Dt[kMaxM][kMaxM];
+  T dhl[kMaxM], dhr[kMaxM];
+  T J[3];
+  T lm[kMaxM], lp[kMaxM];
+  T zeta, nu, inv_t;
+  int n[3];        // elements per direction (n[2] = 1 in 2-D)
+  int ne;          // number of elements
+  int stride;      // elem_stride
+};
+
+}  // namespace acmhd
+
+struct fr_ctx {
+  int device;
+  int dim, order, m, nv, precision, correction;
+  fr_mesh mesh;
+  double zeta, nu, t_r;
+  int ne;
+  size_t stride;       // elem_stride (multiple of 32)
+  int npts;            // m^dim
+  size_t bytes_state;  // nv * npts * stride * sizeof(T)
+  size_t elem_bytes;   // sizeof(T)
+  acmhd::Ops1D ops;
+  acmhd::FrConst<float> cf;
+  acmhd::FrConst<double> cd;
+  // device scratch owned by the context
+  void* trace;         // [2d faces][1+2d slots][m^(d-1)][stride]
+  size_t trace_bytes;
+  void* rk_stage;      // RK4 stage input
+  void* rk_acc;        // RK4 accumulator
+  void* rk_k;          // RK4 stage derivative
+  void* unf_uf;        // unfused: traces of all variables [2d][nv][m^(d-1)][stride]
+  void* unf_f;         // unfused: flux [d][nv][m^d][stride]
+  void* unf_div;       // unfused: divergence [nv][m^d][stride]
+  void* unf_fi;        // unfused: common flux [2d][nv][m^(d-1)][stride]
+  void* host_u;        // fr_rhs_host device staging
+  void* host_r;
+  int* err;            // device error word (bounded waits)
+};
+
+namespace acmhd {
+
+// kernel launchers (defined in the k_*.cu files)
+cudaError_t launch_trace(const fr_ctx* c, const void* U, void* trace, cudaStream_t s);
+cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* trace, void* R,
+                         cudaStream_t s);
+cudaError_t launch_unfused(const fr_ctx* c, const void* U, void* R, cudaStream_t s);
+cudaError_t launch_rk_stage(const fr_ctx* c, int stage, double dtau, void* U,
+                            cudaStream_t s);
+
+}  // namespace acmhd

@@ -1,0 +1,59 @@
+// Face-trace kernel: stage 1 of Table fr_adv ("project solution to x_f"),
+// restricted to the 1 + 2d slots that the normal flux of each face needs.
+//
+// Output layout: Tr[f][s][l][e], f = 2a + side (side 0: the face at -1 of
+// axis a, side 1: the face at +1), s the slot (fr_device.cuh), l the line
+// index along axis a, e the element (stride c.stride).
+//
+// Mapping: a warp covers E consecutive elements (lane -> element, so every
+// global access is one contiguous row) and 32/E lines at once; each thread
+// interpolates one line of each slot variable to both ends.
+#include "fr_device.cuh"
+
+namespace acmhd {
+
+template <int D, int M, typename T, int E>
+__global__ void __launch_bounds__(256)
+trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c) {
+  constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int e = blockIdx.x * E + lane % E;
+  const int sub = lane / E;
+  if (e >= c.ne) return;
+  const size_t S = c.stride;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    for (int l = warp * SUB + sub; l < NL; l += nw * SUB) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const int v = slot_var<D>(s, a);
+        T x[M];
+#pragma unroll
+        for (int t = 0; t < M; ++t)
+          x[t] = __ldg(U + ((size_t)v * NP + line_pt<D, M>(a, l, t)) * S + e);
+        Tr[(((size_t)(2 * a) * NS + s) * NL + l) * S + e] = trace_dot<M>(x, c.lm);
+        Tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e] = trace_dot<M>(x, c.lp);
+      }
+    }
+  }
+}
+
+template <int D, int M, typename T>
+cudaError_t trace_launch(const fr_ctx* ctx, const FrConst<T>& c, const void* U, void* Tr,
+                         cudaStream_t s) {
+  constexpr int E = 32;
+  const int nblk = (ctx->ne + E - 1) / E;
+  trace_kernel<D, M, T, E><<<nblk, 256, 0, s>>>(static_cast<const T*>(U), static_cast<T*>(Tr), c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const fr_ctx* c, const void* U, void* Tr, cudaStream_t s) {
+  if (c->precision == FR_F32) {
+    ACMHD_DISPATCH_DM(c->dim, c->m, return (trace_launch<D_, M_, float>(c, c->cf, U, Tr, s)));
+  } else {
+    ACMHD_DISPATCH_DM(c->dim, c->m, return (trace_launch<D_, M_, double>(c, c->cd, U, Tr, s)));
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace acmhd

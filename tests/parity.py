@@ -1,0 +1,65 @@
+"""Shared helpers for the GPU parity tests (test code; imports the oracle).
+
+Tolerances.  The RHS of a variable is a sum of flux-divergence terms of
+magnitude about J |Dt| |F| that cancel to a much smaller result (by a
+factor up to ~1e5 for the auxiliary equations, whose result is
+(grad u - q)/T).  Floating-point error is proportional to the terms, not
+to the result, so the parity bound for variable v is
+
+    || R_gpu,v - R_oracle,v ||_2  <=  tol * || B_v ||_2,
+    B_v = sum_a J_a sum_k |Dt_ik| |F_a,v,k|  +  |S_v|,
+
+with tol = 1e-12 (FP64) and 2e-5 (FP32), the oracle evaluated in FP64 on
+the identical (already rounded) input values.  Where the result does not
+cancel (noisy inputs) FP64 must also meet the plain relative bound
+|| dR_v || <= 1e-12 || R_oracle,v ||.
+"""
+import numpy as np
+
+from oracle import acmhd, fr
+from oracle.ops1d import Ops1D
+from paper_2107_14027_gb300 import workloads as W
+
+TOL = {32: 2e-5, 64: 1e-12}
+PLAIN_TOL_F64 = 1e-12
+
+
+def term_scale(U, mesh, order, prm, corr="dg"):
+    """RMS over points of B_v, per variable."""
+    ops = Ops1D(order, corr)
+    Dt = ops.D - np.outer(ops.dhl, ops.lm) - np.outer(ops.dhr, ops.lp)
+    G = fr.to_grid(np.asarray(U, dtype=np.float64), mesh, ops.m)
+    d = mesh.d
+    B = np.abs(acmhd.source(G, prm.T))
+    for a in range(d):
+        F = np.abs(acmhd.flux(G, a, prm.zeta, prm.nu, prm.T))
+        B = B + (2.0 / mesh.h[a]) * fr._apply_along(np.abs(Dt), F, 1 + d + a)
+    B = fr.from_grid(B, mesh, ops.m)
+    return np.sqrt(np.mean(B * B, axis=(1, 2)))
+
+
+def errors(R_gpu, R_ref, scale):
+    diff = np.sqrt(np.mean((R_gpu - R_ref) ** 2, axis=(1, 2)))
+    ref = np.sqrt(np.mean(R_ref ** 2, axis=(1, 2)))
+    return diff / scale, diff / np.maximum(ref, 1e-300), ref / scale
+
+
+def assert_parity(R_gpu, R_ref, scale, precision, plain=False, label=""):
+    scaled, rel, cancel = errors(R_gpu, R_ref, scale)
+    tol = TOL[precision]
+    assert np.all(np.isfinite(R_gpu)), f"{label}: non-finite output"
+    assert np.all(scaled <= tol), f"{label}: scaled error {scaled.max():.3e} > {tol} ({scaled})"
+    if plain and precision == 64:
+        sel = cancel > 1e-3   # variables whose result does not cancel
+        assert np.all(rel[sel] <= PLAIN_TOL_F64), f"{label}: relative error {rel[sel].max():.3e}"
+    return scaled, rel
+
+
+def make_case(n, order, zeta=2.5, nu=1.0 / 1600.0, t_r=5e-3, noise=True, seed=W.NOISE_SEED,
+              domain=(-np.pi, np.pi)):
+    d = len(n)
+    lo, hi = (domain[0],) * d, (domain[1],) * d
+    U = W.taylor_green(n, lo, hi, order)
+    if noise:
+        U = W.add_noise(U, seed=seed)
+    return U, fr.Mesh(n, lo, hi), fr.Params(zeta, nu, t_r), lo, hi
