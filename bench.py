@@ -372,6 +372,27 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """A smaller copy of the workload (N^3 elements, same order and
+    variables) for ncu captures: warm-up + steps fused RHS calls only."""
+    import torch
+    from paper_2107_14027_gb300 import abi
+    from paper_2107_14027_gb300 import workloads as W
+    cfg = W.WORKLOADS[WORKLOAD]
+    n = (args.mesh,) * 3
+    U = W.taylor_green(n, cfg["lo"], cfg["hi"], cfg["order"], dtype=np.float32)
+    ctx = abi.fr_create(n, cfg["lo"], cfg["hi"], cfg["order"], 13, cfg["zeta"], cfg["nu"],
+                        cfg["t_r"], abi.FR_F32, abi.FR_CORR_DG)
+    Ud = abi.pack_state(ctx, U, abi.FR_F32)
+    Rd = abi.new_state(ctx, abi.FR_F32)
+    stream = torch.cuda.current_stream()
+    t = _time_loop(lambda: abi.fr_rhs(ctx, Ud, Rd, stream), stream, args.steps, args.warmup, torch)
+    abi.fr_destroy(ctx)
+    dof = int(np.prod(n)) * 64 * 13
+    print(json.dumps({"profile_case": f"hex_p3_{args.mesh}cube", "ms_per_rhs": 1e3 * t / args.steps,
+                      "gdof_s": dof * args.steps / t / 1e9}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,11 +400,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh", type=int, default=None,
+                    help="profiling only: run fr_rhs on an N^3 mesh and print its timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.mesh is not None:
+        run_profile_case(args)
     else:
         run_gpu(args)
 

@@ -39,9 +39,15 @@ def term_scale(U, mesh, order, prm, corr="dg"):
 
 
 def errors(R_gpu, R_ref, scale):
+    """(scaled error, plain relative error, |R| / scale) per variable.  A
+    variable whose terms are all exactly zero (scale 0) must come out exactly
+    zero: its scaled error is then 0 or inf."""
     diff = np.sqrt(np.mean((R_gpu - R_ref) ** 2, axis=(1, 2)))
     ref = np.sqrt(np.mean(R_ref ** 2, axis=(1, 2)))
-    return diff / scale, diff / np.maximum(ref, 1e-300), ref / scale
+    zero = scale == 0.0
+    safe = np.where(zero, 1.0, scale)
+    scaled = np.where(zero, np.where(diff == 0.0, 0.0, np.inf), diff / safe)
+    return scaled, diff / np.maximum(ref, 1e-300), ref / safe
 
 
 def assert_parity(R_gpu, R_ref, scale, precision, plain=False, label=""):
