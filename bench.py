@@ -351,7 +351,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "order": order, "mesh": list(n), "nvars": nv,
                        "elements": int(np.prod(n)), "dof": dof, "precision": "fp32",
-                       "l2": "inputs larger than L2 (state 872 MB, traces 440 MB)",
+                       "l2": "inputs larger than L2 (state 872 MB, traces 705 MB)",
                        "parallelism": f"replicas{world}"},
             "e2e": e2e,
             "roofline": roofline,
