@@ -135,6 +135,32 @@ int fr_rhs_host(fr_ctx* ctx, const void* U_host, void* R_host, void* stream);
  * Uses the context's RK registers.  Asynchronous. */
 int fr_rk_step(fr_ctx* ctx, void* U, double dtau, void* stream);
 
+/* fr_rhs for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of fr_rhs with the same kernels
+ * and the same results.  Some callers must not allocate device memory once
+ * running - e.g. a host application whose own pool allocator reserved the
+ * device's memory at start-up, or a time-critical loop in which a device
+ * allocation (which can synchronise the whole device) is not allowed - and
+ * fr_create allocates.  This call needs no context: it takes the mesh and
+ * parameters of fr_create (same meaning and checks) and the state buffers
+ * of fr_rhs (same layout; elem_stride = n_elem rounded up to a multiple of
+ * 32), and calls no cudaMalloc, cudaFree or other allocating routine.
+ * Its face-trace scratch is one fixed 16 MiB array in the library's device
+ * image, held by every GPU that loads the library until the process exits.
+ * Limit: 2d (1+2d) (p+1)^(d-1) * elem_stride * sizeof(value) <= 16 MiB
+ * (e.g. 6,240 hexahedra at p = 3 in FP32, 3,104 in FP64); larger problems
+ * return FR_EINVAL with the reason in fr_last_error() and launch nothing.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that
+ * first call before any stream capture.  All calls share the one array and
+ * it keeps the previous call's contents (nothing needs clearing: every
+ * entry read is first written by the same call), so calls whose kernels
+ * overlap on the GPU - other streams or host threads - race on it and must
+ * be serialised by the caller.  Asynchronous on `stream`. */
+int fr_rhs_static(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
+                  double t_r, int precision, int correction, const void* U, void* R,
+                  void* stream);
+
 /* Reads the context's device error word after synchronising `stream`;
  * returns FR_ETIMEOUT if a bounded in-kernel wait gave up since the last
  * call (and clears it), else FR_OK or FR_ECUDA. */

@@ -20,7 +20,7 @@ FR_CORR_DG, FR_CORR_G2 = 0, 1
 
 EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_trace", "fr_rhs_volume",
            "fr_rhs_unfused", "fr_rhs_host",
-           "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error"]
+           "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error", "fr_rhs_static"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -55,6 +55,8 @@ def _lib():
             getattr(lib, name).argtypes = [vp, vp, vp, vp]
         lib.fr_trace.argtypes = [vp, vp, vp]
         lib.fr_rk_step.argtypes = [vp, vp, dbl, vp]
+        lib.fr_rhs_static.argtypes = [ctypes.POINTER(fr_mesh), i32, i32, dbl, dbl, dbl, i32, i32,
+                                      vp, vp, vp]
         lib.fr_check.argtypes = [vp, vp]
         lib.fr_strerror.argtypes = [i32]
         lib.fr_strerror.restype = ctypes.c_char_p
@@ -153,6 +155,20 @@ def fr_rhs_host(ctx, U_host, R_host, stream=None):
         return ctypes.c_void_p(x.data_ptr())
     _check(_lib().fr_rhs_host(ctypes.c_void_p(ctx), hp(U_host), hp(R_host), _stream(stream)),
            "fr_rhs_host")
+
+
+def fr_rhs_static(n, lo, hi, order, nvars, zeta, nu, t_r, precision, correction, U, R,
+                  stream=None):
+    """fr_rhs without a context and without any device allocation (the face
+    traces live in the library's fixed 16 MiB device array)."""
+    mesh = make_mesh(n, lo, hi)
+    _check(_lib().fr_rhs_static(ctypes.byref(mesh), int(order), int(nvars), float(zeta),
+                                float(nu), float(t_r), int(precision), int(correction), _ptr(U),
+                                _ptr(R), _stream(stream)), "fr_rhs_static")
+
+
+def fr_last_error():
+    return _lib().fr_last_error().decode()
 
 
 def fr_rk_step(ctx, U, dtau, stream=None):

@@ -90,6 +90,10 @@ bool bad_state_ptr(const void* p) { return p == nullptr || !aligned16(p); }
 
 }  // namespace
 
+void acmhd::set_last_error(const char* msg) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+}
+
 extern "C" {
 
 int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu, double t_r,

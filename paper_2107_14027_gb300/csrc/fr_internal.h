@@ -86,6 +86,9 @@ cudaError_t launch_trace(const fr_ctx* c, const void* U, void* trace, cudaStream
 cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* trace, void* R,
                          cudaStream_t s);
 cudaError_t launch_unfused(const fr_ctx* c, const void* U, void* R, cudaStream_t s);
+// Sets the text that fr_last_error() returns in the calling thread.
+void set_last_error(const char* msg);
+
 cudaError_t launch_rk_stage(const fr_ctx* c, int stage, double dtau, void* U,
                             cudaStream_t s);
 
