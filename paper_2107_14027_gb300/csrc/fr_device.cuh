@@ -83,6 +83,22 @@ __device__ __forceinline__ void slot_flux(const T (&u)[1 + 2 * D], int a, T zeta
   }
 }
 
+// Slot s of the normal flux F_a at point t of a line held as u[slot][point]
+// (same arithmetic as slot_flux, one slot at a time).
+template <int D, int M, typename T>
+__device__ __forceinline__ T point_flux(const T (&u)[1 + 2 * D][M], int t, int s, int a, T zeta,
+                                        T nu, T inv_t) {
+  const T va = u[1 + a][t];
+  if (s == 0) return rn_mul(zeta, va);
+  if (s <= D) {
+    const int i = s - 1;
+    T q = rn_mul(nu, u[1 + D + i][t]);
+    q = (i == a) ? rn_sub(u[0][t], q) : -q;
+    return rn_fma(u[1 + i][t], va, q);
+  }
+  return -rn_mul(u[s - D][t], inv_t);
+}
+
 // Common interface flux on a face with normal +e_a, uL on the low side:
 // mean flux plus Rusanov dissipation (s/2)(uR - uL) on P and V, where
 // s = max(|V_a| + sqrt(V_a^2 + zeta)) over both sides (Sec. 5).
@@ -122,6 +138,43 @@ __device__ __forceinline__ void neighbours(int e, const int* n, int (&nb)[3][2])
   } else {
     nb[2][0] = nb[2][1] = e;
   }
+}
+
+// Work decomposition of the fused kernel: E consecutive elements per CTA
+// (lane -> element, 32/E lines per warp), NW warps, MINB CTAs per SM.
+//  * E: the largest of {32, 16, 8, 4} whose shared memory (P, V and their
+//    partial sums) lets two CTAs share an SM;
+//  * NW: the m^(d-1) lines of a phase come in WT = ceil(lines / (32/E))
+//    warp tasks, spread over at most 12 warps in equal rounds;
+//  * MINB: as many CTAs per SM as shared memory allows, as long as each
+//    thread keeps at least REG_FLOOR registers (the kernel is latency
+//    bound: resident warps keep loads in flight).
+template <int D, int M, typename T>
+struct FusedCfg {
+  static constexpr int NP = ipow<M>(D);
+  static constexpr int NL = ipow<M>(D - 1);
+  static constexpr size_t bytes(int e) { return size_t(2) * (1 + D) * NP * e * sizeof(T); }
+  static constexpr int E = bytes(32) <= 112 * 1024 ? 32
+                           : bytes(16) <= 112 * 1024 ? 16
+                           : bytes(8) <= 112 * 1024 ? 8 : 4;
+  static constexpr size_t SMEM = bytes(E);
+  static constexpr int WT = (NL + 32 / E - 1) / (32 / E);
+  static constexpr int ROUNDS = (WT + 11) / 12;
+  static constexpr int NW = (WT + ROUNDS - 1) / ROUNDS;
+  static constexpr int REG_FLOOR = ((M >= 6) ? 80 : 48) * int(sizeof(T) / 4);
+  static constexpr int SMEM_BLOCKS = int((228 * 1024) / (SMEM + 1024));
+  static constexpr int REG_BLOCKS = 65536 / (NW * 32 * REG_FLOOR);
+  static constexpr int MINB_RAW = SMEM_BLOCKS < REG_BLOCKS ? SMEM_BLOCKS : REG_BLOCKS;
+  static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 8 ? 8 : MINB_RAW);
+};
+
+// x-face exchange between lanes.  The fused kernel keeps E consecutive
+// elements in E consecutive lanes, so the left x-neighbour of element e is
+// the previous lane whenever both sit in the same group of E.  Its trace is
+// then taken from that lane with a shuffle instead of from memory, and the
+// trace kernel does not store it.  Both kernels decide with this predicate.
+__device__ __forceinline__ bool x_pair_on_chip(int e_left, int e_right, int E) {
+  return e_right == e_left + 1 && (e_right % E) != 0;
 }
 
 }  // namespace acmhd

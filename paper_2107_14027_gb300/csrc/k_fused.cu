@@ -27,20 +27,8 @@
 
 namespace acmhd {
 
-template <int D, int M, typename T>
-struct FusedCfg {
-  static constexpr int NP = ipow<M>(D);
-  static constexpr size_t bytes(int e) { return size_t(2) * (1 + D) * NP * e * sizeof(T); }
-  // largest E in {32, 16, 8, 4} whose shared memory fits two CTAs per SM
-  static constexpr int E = bytes(32) <= 112 * 1024 ? 32
-                           : bytes(16) <= 112 * 1024 ? 16
-                           : bytes(8) <= 112 * 1024 ? 8 : 4;
-  static constexpr int NW = 8;
-  static constexpr size_t SMEM = bytes(E);
-};
-
-template <int D, int M, typename T, int E, int NW>
-__global__ void __launch_bounds__(NW * 32)
+template <int D, int M, typename T, int E, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB)
 fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ R,
              const FrConst<T> c) {
   constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
@@ -66,8 +54,11 @@ fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ 
 
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    for (int l = warp * SUB + sub; l < NL; l += NW * SUB) {
-      if (!valid) continue;
+    // the trip count is uniform across the warp (shuffles need every lane)
+    for (int l0 = warp * SUB; l0 < NL; l0 += NW * SUB) {
+      const bool lvalid = l0 + sub < NL;
+      const int l = lvalid ? l0 + sub : NL - 1;
+      const bool act = valid && lvalid;
       // slot values along the line
       T u[NS][M];
 #pragma unroll
@@ -79,37 +70,51 @@ fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ 
         for (int i = 0; i < D; ++i)
           u[1 + D + i][t] = __ldg(U + ((size_t)aux_var<D>(i, a) * NP + pt) * S + e);
       }
-      // common fluxes at the two faces of this line (stage 4)
-      T own_lo[NS], own_hi[NS], nb_lo[NS], nb_hi[NS];
+      // neighbour traces: issued right after the line's own loads.  In the
+      // x phase a neighbour inside the lane group is served by a shuffle
+      // below, so only the others are read from memory.
+      const bool lo_mem = (a != 0) || (act && !x_pair_on_chip(nb[0][0], e, E));
+      const bool hi_mem = (a != 0) || (act && !x_pair_on_chip(e, nb[0][1], E));
+      T nb_lo[NS], nb_hi[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        nb_lo[s] = lo_mem ? __ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S + nb[a][0])
+                          : T(0);
+        nb_hi[s] = hi_mem ? __ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S + nb[a][1])
+                          : T(0);
+      }
+      // own traces, and the common fluxes at the two faces (stage 4)
+      T own_lo[NS], own_hi[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         own_lo[s] = trace_dot<M>(u[s], c.lm);
         own_hi[s] = trace_dot<M>(u[s], c.lp);
-        nb_lo[s] = __ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S + nb[a][0]);
-        nb_hi[s] = __ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S + nb[a][1]);
+      }
+      if (a == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          const T from_left = __shfl_up_sync(0xffffffffu, own_hi[s], 1, E);
+          const T from_right = __shfl_down_sync(0xffffffffu, own_lo[s], 1, E);
+          if (!lo_mem) nb_lo[s] = from_left;
+          if (!hi_mem) nb_hi[s] = from_right;
+        }
       }
       T fl[NS], fr[NS];
       common_flux<D>(nb_lo, own_lo, a, c.zeta, c.nu, c.inv_t, fl);
       common_flux<D>(own_hi, nb_hi, a, c.zeta, c.nu, c.inv_t, fr);
-      // pointwise flux (stage 2)
-      T f[NS][M];
-#pragma unroll
-      for (int t = 0; t < M; ++t) {
-        T ut[NS], ft[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) ut[s] = u[s][t];
-        slot_flux<D>(ut, a, c.zeta, c.nu, c.inv_t, ft);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) f[s][t] = ft[s];
-      }
-      // divergence + correction + negation (stages 3, 5, 6)
+      if (!act) continue;
+      // per slot: pointwise flux (stage 2), then divergence + correction +
+      // negation (stages 3, 5, 6) along the line
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
+        T f[M];
+#pragma unroll
+        for (int t = 0; t < M; ++t) f[t] = point_flux<D>(u, t, s, a, c.zeta, c.nu, c.inv_t);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           T r = fma(c.br[a][i], fr[s], c.bl[a][i] * fl[s]);
 #pragma unroll
-          for (int k = 0; k < M; ++k) r = fma(c.A[a][i][k], f[s][k], r);
+          for (int k = 0; k < M; ++k) r = fma(c.A[a][i][k], f[k], r);
           const int pt = line_pt<D, M>(a, l, i);
           if (s <= D) {
             const int idx = (s * NP + pt) * E + el;
@@ -136,7 +141,7 @@ template <int D, int M, typename T>
 cudaError_t fused_launch(const fr_ctx* ctx, const FrConst<T>& c, const void* U, const void* Tr,
                          void* R, cudaStream_t s) {
   using C = FusedCfg<D, M, T>;
-  auto kern = fused_kernel<D, M, T, C::E, C::NW>;
+  auto kern = fused_kernel<D, M, T, C::E, C::NW, C::MINB>;
   static bool attr_done = false;  // per template instance
   if (!attr_done) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

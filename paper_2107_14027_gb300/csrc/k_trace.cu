@@ -7,12 +7,15 @@
 //
 // Mapping: a warp covers E consecutive elements (lane -> element, so every
 // global access is one contiguous row) and 32/E lines at once; each thread
-// interpolates one line of each slot variable to both ends.
+// interpolates one line of each slot variable to both ends.  x-face traces
+// are stored only for the elements whose x-neighbour will read them from
+// memory (x_pair_on_chip): the fused kernel exchanges the others between
+// lanes.
 #include "fr_device.cuh"
 
 namespace acmhd {
 
-template <int D, int M, typename T, int E>
+template <int D, int M, typename T, int E, int EF>
 __global__ void __launch_bounds__(256)
 trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c) {
   constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
@@ -21,18 +24,32 @@ trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c) {
   const int sub = lane / E;
   if (e >= c.ne) return;
   const size_t S = c.stride;
+  int nb[3][2];
+  neighbours<D>(e, c.n, nb);
+  // x faces: stored only where the fused kernel (EF elements per lane
+  // group) cannot take them from the neighbouring lane
+  const bool need_x_lo = !x_pair_on_chip(nb[0][0], e, EF);
+  const bool need_x_hi = !x_pair_on_chip(e, nb[0][1], EF);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
+    const bool need_lo = (a == 0) ? need_x_lo : true;
+    const bool need_hi = (a == 0) ? need_x_hi : true;
+    if (!need_lo && !need_hi) continue;
     for (int l = warp * SUB + sub; l < NL; l += nw * SUB) {
+      // all loads of the line first, then the interpolations
+      T x[NS][M];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         const int v = slot_var<D>(s, a);
-        T x[M];
 #pragma unroll
         for (int t = 0; t < M; ++t)
-          x[t] = __ldg(U + ((size_t)v * NP + line_pt<D, M>(a, l, t)) * S + e);
-        Tr[(((size_t)(2 * a) * NS + s) * NL + l) * S + e] = trace_dot<M>(x, c.lm);
-        Tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e] = trace_dot<M>(x, c.lp);
+          x[s][t] = __ldg(U + ((size_t)v * NP + line_pt<D, M>(a, l, t)) * S + e);
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (need_lo) Tr[(((size_t)(2 * a) * NS + s) * NL + l) * S + e] = trace_dot<M>(x[s], c.lm);
+        if (need_hi)
+          Tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e] = trace_dot<M>(x[s], c.lp);
       }
     }
   }
@@ -43,7 +60,8 @@ cudaError_t trace_launch(const fr_ctx* ctx, const FrConst<T>& c, const void* U, 
                          cudaStream_t s) {
   constexpr int E = 32;
   const int nblk = (ctx->ne + E - 1) / E;
-  trace_kernel<D, M, T, E><<<nblk, 256, 0, s>>>(static_cast<const T*>(U), static_cast<T*>(Tr), c);
+  trace_kernel<D, M, T, E, FusedCfg<D, M, T>::E>
+      <<<nblk, 256, 0, s>>>(static_cast<const T*>(U), static_cast<T*>(Tr), c);
   return cudaGetLastError();
 }
 
