@@ -74,6 +74,7 @@ enum {
 };
 
 enum { FR_F32 = 32, FR_F64 = 64 };           /* arithmetic precision */
+enum { FR_GUESS_PREVIOUS = 0, FR_GUESS_EXTRAPOLATE = 1 };  /* fr_dual_step guess */
 enum { FR_CORR_DG = 0, FR_CORR_G2 = 1 };     /* correction function (Sec. 2.1) */
 
 /* Create a context.
@@ -160,6 +161,78 @@ int fr_rk_step(fr_ctx* ctx, void* U, double dtau, void* stream);
 int fr_rhs_static(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
                   double t_r, int precision, int correction, const void* U, void* R,
                   void* stream);
+
+/* Pseudo-time iteration of one physical time step (Sec. 5, dual time
+ * stepping): classical RK4 in pseudo time tau on
+ *     dU/dtau = R_tau(U) = R(U) - I_V (a0 V + a1 V^n + a2 V^{n-1}) / dt,
+ * where I_V selects the velocity equations (Eq. acmhd_nd: the physical time
+ * derivative acts on V only) and (a0, a1, a2) = (1, -1, 0) for BDF1 or
+ * (3/2, -2, 1/2) for BDF2, until the residual - the RMS over all velocity
+ * degrees of freedom of R_tau(U) - is below tol.
+ *   U        work state (context precision; device), in/out.  Its P and
+ *            auxiliary rows are the initial guess; its velocity rows are
+ *            overwritten from V.
+ *   V        velocity master in FP64: rows 1..d of a state, i.e.
+ *            d * (p+1)^d * elem_stride doubles (device), in/out: the initial
+ *            guess on entry, the converged velocity on return.  The BDF source,
+ *            the velocity part of the RK4 update and the residual are FP64.
+ *   Vn, Vnm1 FP64 velocity at t^n and t^{n-1} (same layout; Vnm1 unused for
+ *            bdf_order 1).  dt > 0, dtau > 0 the physical and pseudo steps.
+ *   check_every  the residual is evaluated (from the first RK stage of the
+ *            step, no extra RHS) every check_every iterations and after the
+ *            last; each check reads one double back to the host and is the
+ *            call's only synchronisation.
+ *   stall    if > 0, also stop (FR_ENOCONV) when a check finds the residual
+ *            above stall times the previous check's (0 disables).
+ * Returns FR_OK (converged, *res < tol), FR_ENOCONV (max_iter reached or
+ * stalled; U and V hold the last iterate), FR_ENONFINITE (residual NaN/Inf).  *iters
+ * and *res (if non-NULL) receive the iteration count and last residual.
+ * Allocates its FP64 registers on first use. */
+int fr_pseudo_solve(fr_ctx* ctx, void* U, double* V, const double* Vn, const double* Vnm1,
+                    double dt, int bdf_order, double dtau, double tol, int max_iter,
+                    int check_every, double stall, int* iters, double* res, void* stream);
+
+/* Physical time stepping with context-owned history (three levels of the
+ * state and of the FP64 velocity).  fr_dual_init stores U as level n (its
+ * velocity widened to FP64) and allocates the history on first use.
+ * fr_dual_step advances one step: initial guess (FR_GUESS_PREVIOUS: level
+ * n; FR_GUESS_EXTRAPOLATE: the extrapolation through the stored levels,
+ * 2U^n - U^{n-1} or 3U^n - 3U^{n-1} + U^{n-2}), fr_pseudo_solve with BDF1 on
+ * the first step and BDF2 afterwards, then the new level enters the history
+ * (also when the solve returns FR_ENOCONV, which is passed on).  U receives
+ * the new level.
+ *
+ * Mixed precision: FP32 arithmetic cannot bring the residual below its own
+ * rounding floor (the FP32 RHS of the stored state).  With `refine` set to
+ * an FR_F64 context on the same mesh, order, correction and parameters, the
+ * iterations in ctx stop at tol_switch (or when the residual stalls: a check
+ * finds it above 0.99 times the previous check's) and
+ * continue on `refine` (work state U_refine, device, refine's layout) from
+ * the widened state until tol; the result is narrowed back into U.  The
+ * FP64 velocity master and the history stay in ctx.
+ * fr_dual_velocity copies the newest FP64 velocity level into V (device). */
+typedef struct fr_dual_opts {
+    double dt, dtau;      /* physical and pseudo time steps (> 0) */
+    double tol;           /* residual tolerance (RMS of R_tau over velocity DOFs) */
+    int max_iter;         /* pseudo iterations per physical step, both phases */
+    int check_every;      /* residual check interval (>= 1) */
+    int guess;            /* FR_GUESS_* */
+    fr_ctx* refine;       /* NULL, or the FP64 refinement context */
+    void* U_refine;       /* refine's work state */
+    double tol_switch;    /* residual at which ctx hands over to refine */
+} fr_dual_opts;
+
+typedef struct fr_dual_stats {
+    int iters;            /* pseudo iterations in ctx */
+    int iters_refine;     /* pseudo iterations in refine */
+    double res;           /* final residual */
+    double res_switch;    /* residual when ctx handed over (or final) */
+} fr_dual_stats;
+
+int fr_dual_init(fr_ctx* ctx, const void* U, void* stream);
+int fr_dual_step(fr_ctx* ctx, void* U, const fr_dual_opts* opts, fr_dual_stats* stats,
+                 void* stream);
+int fr_dual_velocity(const fr_ctx* ctx, double* V, void* stream);
 
 /* Reads the context's device error word after synchronising `stream`;
  * returns FR_ETIMEOUT if a bounded in-kernel wait gave up since the last

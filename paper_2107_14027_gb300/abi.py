@@ -17,15 +17,29 @@ LIB_PATH = os.path.join(HERE, "libacmhd_fr.so")
 FR_OK, FR_EINVAL, FR_ECUDA, FR_ENOCONV, FR_ENONFINITE, FR_ENOMEM, FR_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 FR_F32, FR_F64 = 32, 64
 FR_CORR_DG, FR_CORR_G2 = 0, 1
+FR_GUESS_PREVIOUS, FR_GUESS_EXTRAPOLATE = 0, 1
 
 EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_trace", "fr_rhs_volume",
            "fr_rhs_unfused", "fr_rhs_host",
-           "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error", "fr_rhs_static"]
+           "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error", "fr_rhs_static",
+           "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity"]
 
 
 class fr_mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class fr_dual_opts(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("dtau", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int), ("guess", ctypes.c_int),
+                ("refine", ctypes.c_void_p), ("U_refine", ctypes.c_void_p),
+                ("tol_switch", ctypes.c_double)]
+
+
+class fr_dual_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("iters_refine", ctypes.c_int), ("res", ctypes.c_double),
+                ("res_switch", ctypes.c_double)]
 
 
 class FrError(RuntimeError):
@@ -58,6 +72,13 @@ def _lib():
         lib.fr_rhs_static.argtypes = [ctypes.POINTER(fr_mesh), i32, i32, dbl, dbl, dbl, i32, i32,
                                       vp, vp, vp]
         lib.fr_check.argtypes = [vp, vp]
+        ip, dp = ctypes.POINTER(i32), ctypes.POINTER(dbl)
+        lib.fr_pseudo_solve.argtypes = [vp, vp, vp, vp, vp, dbl, i32, dbl, dbl, i32, i32, dbl, ip,
+                                        dp, vp]
+        lib.fr_dual_init.argtypes = [vp, vp, vp]
+        lib.fr_dual_step.argtypes = [vp, vp, ctypes.POINTER(fr_dual_opts),
+                                     ctypes.POINTER(fr_dual_stats), vp]
+        lib.fr_dual_velocity.argtypes = [vp, vp, vp]
         lib.fr_strerror.argtypes = [i32]
         lib.fr_strerror.restype = ctypes.c_char_p
         lib.fr_last_error.argtypes = []
@@ -174,6 +195,56 @@ def fr_last_error():
 def fr_rk_step(ctx, U, dtau, stream=None):
     _check(_lib().fr_rk_step(ctypes.c_void_p(ctx), _ptr(U), float(dtau), _stream(stream)),
            "fr_rk_step")
+
+
+def fr_pseudo_solve(ctx, U, V, Vn, Vnm1, dt, bdf_order, dtau, tol, max_iter, check_every=1,
+                    stall=0.0, stream=None, allow_noconv=False):
+    """Returns (status, iterations, residual).  FR_ENOCONV raises unless
+    allow_noconv is set."""
+    it, res = ctypes.c_int(), ctypes.c_double()
+    st = _lib().fr_pseudo_solve(ctypes.c_void_p(ctx), _ptr(U), _ptr(V), _ptr(Vn),
+                                _ptr(Vnm1) if Vnm1 is not None else None, float(dt),
+                                int(bdf_order), float(dtau), float(tol), int(max_iter),
+                                int(check_every), float(stall), ctypes.byref(it),
+                                ctypes.byref(res), _stream(stream))
+    if not (st == FR_OK or (allow_noconv and st == FR_ENOCONV)):
+        _check(st, "fr_pseudo_solve")
+    return st, it.value, res.value
+
+
+def fr_dual_init(ctx, U, stream=None):
+    _check(_lib().fr_dual_init(ctypes.c_void_p(ctx), _ptr(U), _stream(stream)), "fr_dual_init")
+
+
+def fr_dual_step(ctx, U, dt, dtau, tol, max_iter, check_every=1, guess=FR_GUESS_EXTRAPOLATE,
+                 refine=None, U_refine=None, tol_switch=0.0, stream=None, allow_noconv=False):
+    """Returns (status, fr_dual_stats)."""
+    opts = fr_dual_opts(float(dt), float(dtau), float(tol), int(max_iter), int(check_every),
+                        int(guess), refine, U_refine.data_ptr() if U_refine is not None else None,
+                        float(tol_switch))
+    stats = fr_dual_stats()
+    st = _lib().fr_dual_step(ctypes.c_void_p(ctx), _ptr(U), ctypes.byref(opts),
+                             ctypes.byref(stats), _stream(stream))
+    if not (st == FR_OK or (allow_noconv and st == FR_ENOCONV)):
+        _check(st, "fr_dual_step")
+    return st, stats
+
+
+def fr_dual_velocity(ctx, V, stream=None):
+    _check(_lib().fr_dual_velocity(ctypes.c_void_p(ctx), _ptr(V), _stream(stream)),
+           "fr_dual_velocity")
+
+
+def new_velocity(ctx, dim, order, device="cuda"):
+    """FP64 velocity rows of a state: d * (p+1)^d rows of elem_stride."""
+    import torch
+    stride, _, _ = fr_layout(ctx)
+    return torch.zeros((dim * (order + 1) ** dim, stride), dtype=torch.float64, device=device)
+
+
+def velocity_rows(U, dim, npts):
+    """The velocity rows of a packed state tensor (a view)."""
+    return U[npts:(1 + dim) * npts]
 
 
 def fr_check(ctx, stream=None):

@@ -88,6 +88,33 @@ int ensure_unfused(fr_ctx* c) {
 
 bool bad_state_ptr(const void* p) { return p == nullptr || !aligned16(p); }
 
+size_t vel_doubles(const fr_ctx* c) { return (size_t)c->dim * c->npts * c->stride; }
+
+int ensure_dual(fr_ctx* c) {
+  const size_t vb = vel_doubles(c) * sizeof(double);
+  int st;
+  if ((st = alloc_zeroed((void**)&c->dual_vs, vb, "dual registers")) != FR_OK) return st;
+  if ((st = alloc_zeroed((void**)&c->dual_vacc, vb, "dual registers")) != FR_OK) return st;
+  if ((st = alloc_zeroed((void**)&c->dual_c, vb, "dual registers")) != FR_OK) return st;
+  if ((st = alloc_zeroed((void**)&c->dual_partial,
+                         acmhd::dual_norm_blocks(c) * sizeof(double), "dual registers")) != FR_OK)
+    return st;
+  return alloc_zeroed((void**)&c->dual_res, sizeof(double), "dual registers");
+}
+
+int ensure_history(fr_ctx* c) {
+  int st;
+  if ((st = alloc_zeroed((void**)&c->dual_v, vel_doubles(c) * sizeof(double), "history")) != FR_OK)
+    return st;
+  for (int i = 0; i < 3; ++i) {
+    if ((st = alloc_zeroed(&c->hist_u[i], c->bytes_state, "history")) != FR_OK) return st;
+    if ((st = alloc_zeroed((void**)&c->hist_v[i], vel_doubles(c) * sizeof(double), "history")) !=
+        FR_OK)
+      return st;
+  }
+  return FR_OK;
+}
+
 }  // namespace
 
 void acmhd::set_last_error(const char* msg) {
@@ -167,7 +194,10 @@ void fr_destroy(fr_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   void* bufs[] = {c->trace, c->rk_stage, c->rk_acc, c->rk_k, c->unf_uf, c->unf_f,
-                  c->unf_div, c->unf_fi, c->host_u, c->host_r, c->err};
+                  c->unf_div, c->unf_fi, c->host_u, c->host_r, c->err,
+                  c->dual_vs, c->dual_vacc, c->dual_c, c->dual_partial, c->dual_res, c->dual_v,
+                  c->hist_u[0], c->hist_u[1], c->hist_u[2],
+                  c->hist_v[0], c->hist_v[1], c->hist_v[2]};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -238,6 +268,171 @@ int fr_rk_step(fr_ctx* c, void* U, double dtau, void* stream) {
     if (st != FR_OK) return st;
   }
   return FR_OK;
+}
+
+int fr_pseudo_solve(fr_ctx* c, void* U, double* V, const double* Vn, const double* Vnm1,
+                    double dt, int bdf_order, double dtau, double tol, int max_iter,
+                    int check_every, double stall, int* iters, double* res, void* stream) {
+  if (!c || bad_state_ptr(U) || bad_state_ptr(V) || bad_state_ptr(Vn)) return FR_EINVAL;
+  if (bdf_order != 1 && bdf_order != 2) return FR_EINVAL;
+  if (bdf_order == 2 && bad_state_ptr(Vnm1)) return FR_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt) || !(dtau > 0.0) || !std::isfinite(dtau) ||
+      !(tol >= 0.0) || max_iter < 0 || check_every < 1 || !(stall >= 0.0))
+    return FR_EINVAL;
+  int st = ensure_rk(c);
+  if (st == FR_OK) st = ensure_dual(c);
+  if (st != FR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // BDF coefficients: dV/dt ~ (a0 V + a1 V^n + a2 V^{n-1}) / dt
+  const double a0 = bdf_order == 1 ? 1.0 : 1.5;
+  const double a1 = bdf_order == 1 ? -1.0 : -2.0;
+  const double a2 = bdf_order == 1 ? 0.0 : 0.5;
+  st = cuda_status(acmhd::launch_bdf_const(c, -a1 / dt, -a2 / dt, Vn, bdf_order == 2 ? Vnm1 : Vn,
+                                           c->dual_c, s),
+                   "bdf source");
+  if (st == FR_OK) st = cuda_status(acmhd::launch_sync_velocity(c, V, U, s), "velocity sync");
+  if (st != FR_OK) return st;
+  const double count = (double)c->dim * c->npts * c->ne;
+  double last = NAN, prev = INFINITY;
+  bool converged = false;
+  int it = 0;
+  for (;;) {
+    if ((st = fr_rhs(c, U, c->rk_k, stream)) != FR_OK) return st;
+    st = cuda_status(acmhd::launch_dual_stage(c, 0, dtau, a0 / dt, U, V, c->dual_c,
+                                              c->dual_partial, s),
+                     "dual stage");
+    if (st != FR_OK) return st;
+    if (it % check_every == 0 || it == max_iter) {
+      st = cuda_status(acmhd::launch_norm_final(c, c->dual_partial, count, c->dual_res, s),
+                       "residual norm");
+      if (st == FR_OK)
+        st = cuda_status(cudaMemcpyAsync(&last, c->dual_res, sizeof(double),
+                                         cudaMemcpyDeviceToHost, s),
+                         "read residual");
+      if (st == FR_OK) st = cuda_status(cudaStreamSynchronize(s), "stream synchronize");
+      if (st != FR_OK) return st;
+      if (!std::isfinite(last)) {
+        if (iters) *iters = it;
+        if (res) *res = last;
+        return FR_ENONFINITE;
+      }
+      if (last < tol) {
+        converged = true;
+        break;
+      }
+      // stalled: the residual no longer drops by the factor `stall` per check
+      if (stall > 0.0 && it > 0 && last > stall * prev) break;
+      prev = last;
+    }
+    if (it == max_iter) break;
+    for (int stage = 1; stage < 4; ++stage) {
+      if ((st = fr_rhs(c, c->rk_stage, c->rk_k, stream)) != FR_OK) return st;
+      st = cuda_status(acmhd::launch_dual_stage(c, stage, dtau, a0 / dt, U, V, c->dual_c,
+                                                c->dual_partial, s),
+                       "dual stage");
+      if (st != FR_OK) return st;
+    }
+    ++it;
+  }
+  if (iters) *iters = it;
+  if (res) *res = last;
+  return converged ? FR_OK : FR_ENOCONV;
+}
+
+int fr_dual_init(fr_ctx* c, const void* U, void* stream) {
+  if (!c || bad_state_ptr(U)) return FR_EINVAL;
+  int st = ensure_history(c);
+  if (st != FR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)c->nv * c->npts * c->stride;
+  const size_t vel0 = (size_t)c->npts * c->stride;
+  c->hist_head = 0;
+  st = cuda_status(acmhd::launch_combine3(c, c->precision, n, 1.0, 0.0, 0.0, U, nullptr, nullptr,
+                                          c->hist_u[0], s),
+                   "history");
+  // FP64 velocity level from the state's velocity rows
+  if (st == FR_OK)
+    st = cuda_status(acmhd::launch_widen_velocity(c, U, c->hist_v[0], s), "history");
+  if (st != FR_OK) return st;
+  c->hist_levels = 1;
+  return FR_OK;
+}
+
+int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, void* stream) {
+  if (!c || bad_state_ptr(U) || !o || c->hist_levels < 1) return FR_EINVAL;
+  if (o->guess != FR_GUESS_PREVIOUS && o->guess != FR_GUESS_EXTRAPOLATE) return FR_EINVAL;
+  fr_ctx* rf = o->refine;
+  if (rf) {
+    // the refinement context must be the FP64 twin of this one
+    if (rf->precision != FR_F64 || rf->dim != c->dim || rf->order != c->order ||
+        rf->ne != c->ne || rf->stride != c->stride || rf->correction != c->correction ||
+        rf->zeta != c->zeta || rf->nu != c->nu || rf->t_r != c->t_r ||
+        std::memcmp(rf->mesh.n, c->mesh.n, sizeof(c->mesh.n)) != 0 ||
+        bad_state_ptr(o->U_refine) || !(o->tol_switch >= 0.0))
+      return FR_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int L = c->hist_levels;
+  const int h0 = c->hist_head, h1 = (h0 + 2) % 3, h2 = (h0 + 1) % 3;  // levels n, n-1, n-2
+  const size_t n = (size_t)c->nv * c->npts * c->stride;
+  const size_t nv = vel_doubles(c);
+  // initial guess of the new level: the previous level, or the polynomial
+  // extrapolation through the stored levels (linear with two, quadratic with
+  // three: 3 U^n - 3 U^{n-1} + U^{n-2})
+  double w0 = 1.0, w1 = 0.0, w2 = 0.0;
+  if (o->guess == FR_GUESS_EXTRAPOLATE && L == 2) w0 = 2.0, w1 = -1.0;
+  if (o->guess == FR_GUESS_EXTRAPOLATE && L == 3) w0 = 3.0, w1 = -3.0, w2 = 1.0;
+  int st = cuda_status(acmhd::launch_combine3(c, c->precision, n, w0, w1, w2, c->hist_u[h0],
+                                              c->hist_u[h1], c->hist_u[h2], U, s),
+                       "initial guess");
+  if (st == FR_OK)
+    st = cuda_status(acmhd::launch_combine3(c, FR_F64, nv, w0, w1, w2, c->hist_v[h0],
+                                            c->hist_v[h1], c->hist_v[h2], c->dual_v, s),
+                     "initial guess");
+  if (st != FR_OK) return st;
+  const int order = L >= 2 ? 2 : 1;
+  fr_dual_stats stats = {0, 0, NAN, NAN};
+  // iterations in this context's precision; with a refinement context they
+  // stop at tol_switch or when the residual stalls
+  const double tol1 = rf ? (o->tol > o->tol_switch ? o->tol : o->tol_switch) : o->tol;
+  int solve = fr_pseudo_solve(c, U, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
+                              o->dtau, tol1, o->max_iter, o->check_every, rf ? 0.99 : 0.0,
+                              &stats.iters, &stats.res, stream);
+  if (solve != FR_OK && solve != FR_ENOCONV) return solve;
+  stats.res_switch = stats.res;
+  if (rf && !(stats.res < o->tol) && stats.iters < o->max_iter) {
+    st = cuda_status(acmhd::launch_convert(c, n, c->precision, U, FR_F64, o->U_refine, s),
+                     "widen state");
+    if (st != FR_OK) return st;
+    solve = fr_pseudo_solve(rf, o->U_refine, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt,
+                            order, o->dtau, o->tol, o->max_iter - stats.iters, o->check_every,
+                            0.0, &stats.iters_refine, &stats.res, stream);
+    if (solve != FR_OK && solve != FR_ENOCONV) return solve;
+    st = cuda_status(acmhd::launch_convert(c, n, FR_F64, o->U_refine, c->precision, U, s),
+                     "narrow state");
+    if (st != FR_OK) return st;
+  }
+  if (out) *out = stats;
+  // the new level replaces level n-2 in the ring
+  const int hn = (h0 + 1) % 3;
+  st = cuda_status(acmhd::launch_combine3(c, c->precision, n, 1.0, 0.0, 0.0, U, nullptr, nullptr,
+                                          c->hist_u[hn], s),
+                   "history");
+  if (st == FR_OK)
+    st = cuda_status(cudaMemcpyAsync(c->hist_v[hn], c->dual_v, nv * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s),
+                     "history");
+  if (st != FR_OK) return st;
+  c->hist_head = hn;
+  c->hist_levels = L < 3 ? L + 1 : 3;
+  return solve;
+}
+
+int fr_dual_velocity(const fr_ctx* c, double* V, void* stream) {
+  if (!c || bad_state_ptr(V) || c->hist_levels < 1) return FR_EINVAL;
+  return cuda_status(cudaMemcpyAsync(V, c->hist_v[c->hist_head], vel_doubles(c) * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)),
+                     "copy velocity");
 }
 
 int fr_check(fr_ctx* c, void* stream) {

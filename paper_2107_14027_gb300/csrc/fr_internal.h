@@ -77,6 +77,17 @@ struct fr_ctx {
   void* host_u;        // fr_rhs_host device staging
   void* host_r;
   int* err;            // device error word (bounded waits)
+  // dual time stepping (FP64 velocity rows: dim * npts * stride doubles)
+  double* dual_vs;     // RK4 stage velocity
+  double* dual_vacc;   // RK4 velocity accumulator
+  double* dual_c;      // BDF constant part -(a1 V^n + a2 V^{n-1}) / dt
+  double* dual_partial;  // residual partial sums (one per block)
+  double* dual_res;    // residual (one double)
+  double* dual_v;      // velocity master of fr_dual_step
+  void* hist_u[3];     // physical-time levels of the state (precision T)
+  double* hist_v[3];   // physical-time levels of the velocity (FP64)
+  int hist_head;       // slot of level n
+  int hist_levels;     // number of valid levels (0..3)
 };
 
 namespace acmhd {
@@ -86,6 +97,20 @@ cudaError_t launch_trace(const fr_ctx* c, const void* U, void* trace, cudaStream
 cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* trace, void* R,
                          cudaStream_t s);
 cudaError_t launch_unfused(const fr_ctx* c, const void* U, void* R, cudaStream_t s);
+int dual_norm_blocks(const fr_ctx* c);
+cudaError_t launch_sync_velocity(const fr_ctx* c, const double* V, void* U, cudaStream_t s);
+cudaError_t launch_widen_velocity(const fr_ctx* c, const void* U, double* V, cudaStream_t s);
+cudaError_t launch_bdf_const(const fr_ctx* c, double c1, double c2, const double* Vn,
+                             const double* Vnm1, double* C, cudaStream_t s);
+cudaError_t launch_dual_stage(const fr_ctx* c, int stage, double dtau, double a0dt, void* U,
+                              double* V, const double* C, double* partial, cudaStream_t s);
+cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, double count, double* out,
+                              cudaStream_t s);
+cudaError_t launch_convert(const fr_ctx* c, size_t n, int prec_in, const void* x, int prec_out,
+                           void* y, cudaStream_t s);
+cudaError_t launch_combine3(const fr_ctx* c, int precision, size_t n, double c0, double c1,
+                            double c2, const void* x0, const void* x1, const void* x2, void* out,
+                            cudaStream_t s);
 // Sets the text that fr_last_error() returns in the calling thread.
 void set_last_error(const char* msg);
 
