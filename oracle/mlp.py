@@ -1,0 +1,107 @@
+"""Per-element MLP for the learned initial guess, in plain FP64 (test infrastructure).
+
+The paper has no learned component; this follows the build's own
+definition of the learned guess of a physical time step:
+
+  features   x_e = [U^n_e / s, U^{n-1}_e / s, U^{n-2}_e / s]  (element e, each
+             level flattened as (variable, point), s the per-variable input
+             scale), K = 3 n_v (p+1)^d values;
+  network    h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3;
+  guess      U^{n+1}_e ~ U*_e + t (.) y, with the plain extrapolation
+             U* = 3 U^n - 3 U^{n-1} + U^{n-2} and per-variable output scale t;
+  loss       mean over samples and outputs of (y - (U^{n+1} - U*)/t)^2;
+  training   Adam (beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the full batch.
+
+Matrices act on columns: W is (out x in), a batch is stored with samples
+as columns (X is K x B), matching the element-fastest state layout.
+
+Pins (tests/test_oracle_mlp.py): backward against central finite
+differences; a network built to represent a known piecewise-linear map;
+Adam's first step moves every parameter by lr times the sign of its
+gradient; features/targets reproduce the extrapolation identity on data
+that is quadratic in time.
+"""
+import numpy as np
+
+
+def forward(params, X):
+    """params = [(W1, b1), (W2, b2), (W3, b3)]; X is K x B.  Returns (Y, cache)."""
+    (W1, b1), (W2, b2), (W3, b3) = params
+    Z1 = W1 @ X + b1[:, None]
+    H1 = np.maximum(Z1, 0.0)
+    Z2 = W2 @ H1 + b2[:, None]
+    H2 = np.maximum(Z2, 0.0)
+    Y = W3 @ H2 + b3[:, None]
+    return Y, (X, Z1, H1, Z2, H2)
+
+
+def loss(Y, Tgt):
+    return float(np.mean((Y - Tgt) ** 2))
+
+
+def backward(params, cache, Y, Tgt):
+    """Gradients of loss(Y, Tgt) with respect to all parameters."""
+    (W1, b1), (W2, b2), (W3, b3) = params
+    X, Z1, H1, Z2, H2 = cache
+    dY = 2.0 * (Y - Tgt) / Y.size
+    dW3 = dY @ H2.T
+    db3 = dY.sum(axis=1)
+    dH2 = W3.T @ dY
+    dZ2 = dH2 * (Z2 > 0.0)
+    dW2 = dZ2 @ H1.T
+    db2 = dZ2.sum(axis=1)
+    dH1 = W2.T @ dZ2
+    dZ1 = dH1 * (Z1 > 0.0)
+    dW1 = dZ1 @ X.T
+    db1 = dZ1.sum(axis=1)
+    return [(dW1, db1), (dW2, db2), (dW3, db3)]
+
+
+class Adam:
+    """Adam on a list of (W, b) layers."""
+
+    def __init__(self, params, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.lr, self.b1, self.b2, self.eps = lr, beta1, beta2, eps
+        self.m = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
+        self.v = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
+        self.t = 0
+
+    def step(self, params, grads):
+        self.t += 1
+        out = []
+        for i in range(len(params)):
+            layer = []
+            for j in range(2):
+                p, g = params[i][j], grads[i][j]
+                self.m[i][j] = self.b1 * self.m[i][j] + (1.0 - self.b1) * g
+                self.v[i][j] = self.b2 * self.v[i][j] + (1.0 - self.b2) * g * g
+                mh = self.m[i][j] / (1.0 - self.b1 ** self.t)
+                vh = self.v[i][j] / (1.0 - self.b2 ** self.t)
+                layer.append(p - self.lr * mh / (np.sqrt(vh) + self.eps))
+            out.append(tuple(layer))
+        return out
+
+
+def features(Un, Unm1, Unm2, in_scale, elems):
+    """K x B feature matrix of the listed elements; states are [nv, npts, ne]."""
+    s = np.asarray(in_scale, dtype=np.float64)[:, None, None]
+    parts = [(U[:, :, elems] / s).reshape(-1, len(elems)) for U in (Un, Unm1, Unm2)]
+    return np.concatenate(parts, axis=0)
+
+
+def extrapolate(Un, Unm1, Unm2):
+    return 3.0 * Un - 3.0 * Unm1 + Unm2
+
+
+def targets(Unp1, Un, Unm1, Unm2, out_scale, elems):
+    """(n_v npts) x B normalised corrections to the plain extrapolation."""
+    t = np.asarray(out_scale, dtype=np.float64)[:, None, None]
+    D = (Unp1 - extrapolate(Un, Unm1, Unm2))[:, :, elems] / t
+    return D.reshape(-1, len(elems))
+
+
+def apply_guess(Y, Un, Unm1, Unm2, out_scale):
+    """Guess for every element from the network output Y ((n_v npts) x ne)."""
+    nv, npts, ne = Un.shape
+    t = np.asarray(out_scale, dtype=np.float64)[:, None, None]
+    return extrapolate(Un, Unm1, Unm2) + t * Y.reshape(nv, npts, ne)
