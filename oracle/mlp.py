@@ -3,9 +3,14 @@
 The paper has no learned component; this follows the build's own
 definition of the learned guess of a physical time step:
 
-  features   x_e = [U^n_e / s, U^{n-1}_e / s, U^{n-2}_e / s]  (element e, each
-             level flattened as (variable, point), s the per-variable input
-             scale), K = 3 n_v (p+1)^d values;
+  features   x_e = [U^n_e / s0, (U^n - U^{n-1})_e / s1,
+                    (U^n - 2 U^{n-1} + U^{n-2})_e / s2]
+             (element e, each block flattened as (variable, point), s0, s1, s2
+             per-variable scales), K = 3 n_v (p+1)^d values.  This is an
+             invertible linear map of the three previous levels: the network
+             sees the same information, but each block is O(1) after scaling,
+             so BF16 operands keep the small time differences that a BF16
+             copy of the raw levels would round away;
   network    h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3;
   guess      U^{n+1}_e ~ U*_e + t (.) y, with the plain extrapolation
              U* = 3 U^n - 3 U^{n-1} + U^{n-2} and per-variable output scale t;
@@ -82,10 +87,14 @@ class Adam:
         return out
 
 
-def features(Un, Unm1, Unm2, in_scale, elems):
-    """K x B feature matrix of the listed elements; states are [nv, npts, ne]."""
-    s = np.asarray(in_scale, dtype=np.float64)[:, None, None]
-    parts = [(U[:, :, elems] / s).reshape(-1, len(elems)) for U in (Un, Unm1, Unm2)]
+def features(Un, Unm1, Unm2, scales, elems):
+    """K x B feature matrix of the listed elements; states are [nv, npts, ne],
+    scales = (s0, s1, s2), each of length nv."""
+    blocks = (Un, Un - Unm1, Un - 2.0 * Unm1 + Unm2)
+    parts = []
+    for B, s in zip(blocks, scales):
+        s = np.asarray(s, dtype=np.float64)[:, None, None]
+        parts.append((B[:, :, elems] / s).reshape(-1, len(elems)))
     return np.concatenate(parts, axis=0)
 
 

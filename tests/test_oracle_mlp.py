@@ -80,8 +80,11 @@ def test_extrapolation_targets_vanish_for_quadratic_histories():
     U = [a + b * t + c * t * t for t in (0.0, 1.0, 2.0, 3.0)]
     tg = mlp.targets(U[3], U[2], U[1], U[0], np.ones(7), elems=[0, 2, 3])
     np.testing.assert_allclose(tg, 0.0, atol=1e-12)
-    X = mlp.features(U[2], U[1], U[0], 2.0 * np.ones(7), elems=[1])
+    X = mlp.features(U[2], U[1], U[0], (2.0 * np.ones(7), np.ones(7), 0.5 * np.ones(7)), elems=[1])
     assert X.shape == (3 * 7 * 9, 1)
     np.testing.assert_allclose(X[: 7 * 9, 0], U[2][:, :, 1].reshape(-1) / 2.0)
+    # for a quadratic history the difference blocks are b + c(2t-1) and 2c
+    np.testing.assert_allclose(X[7 * 9: 14 * 9, 0], (b + 3.0 * c)[:, :, 1].reshape(-1), atol=1e-12)
+    np.testing.assert_allclose(X[14 * 9:, 0], (2.0 * c / 0.5)[:, :, 1].reshape(-1), atol=1e-12)
     G = mlp.apply_guess(np.zeros((7 * 9, 4)), U[2], U[1], U[0], np.ones(7))
     np.testing.assert_allclose(G, U[3], atol=1e-12)
