@@ -74,7 +74,9 @@ enum {
 };
 
 enum { FR_F32 = 32, FR_F64 = 64 };           /* arithmetic precision */
-enum { FR_GUESS_PREVIOUS = 0, FR_GUESS_EXTRAPOLATE = 1 };  /* fr_dual_step guess */
+enum { FR_GUESS_PREVIOUS = 0, FR_GUESS_EXTRAPOLATE = 1, FR_GUESS_MLP = 2 };  /* fr_dual_step guess */
+
+typedef struct fr_mlp fr_mlp;
 enum { FR_CORR_DG = 0, FR_CORR_G2 = 1 };     /* correction function (Sec. 2.1) */
 
 /* Create a context.
@@ -200,7 +202,10 @@ int fr_pseudo_solve(fr_ctx* ctx, void* U, double* V, const double* Vn, const dou
  * 2U^n - U^{n-1} or 3U^n - 3U^{n-1} + U^{n-2}), fr_pseudo_solve with BDF1 on
  * the first step and BDF2 afterwards, then the new level enters the history
  * (also when the solve returns FR_ENOCONV, which is passed on).  U receives
- * the new level.
+ * the new level.  FR_GUESS_MLP: the extrapolated guess and the network's
+ * guess (opts->mlp, three stored levels needed) are both evaluated - one RHS
+ * and residual each - and the one with the smaller residual is iterated, so
+ * the tolerance decides convergence exactly as without the network.
  *
  * Mixed precision: FP32 arithmetic cannot bring the residual below its own
  * rounding floor (the FP32 RHS of the stored state).  With `refine` set to
@@ -220,6 +225,7 @@ typedef struct fr_dual_opts {
     fr_ctx* refine;       /* NULL, or the FP64 refinement context */
     void* U_refine;       /* refine's work state */
     double tol_switch;    /* residual at which ctx hands over to refine */
+    fr_mlp* mlp;          /* trained network for FR_GUESS_MLP */
 } fr_dual_opts;
 
 typedef struct fr_dual_stats {
@@ -227,12 +233,61 @@ typedef struct fr_dual_stats {
     int iters_refine;     /* pseudo iterations in refine */
     double res;           /* final residual */
     double res_switch;    /* residual when ctx handed over (or final) */
+    int guess_used;       /* FR_GUESS_* actually used (the MLP guess falls back) */
+    double res_guess[2];  /* FR_GUESS_MLP: initial residual of [extrapolation, network] */
 } fr_dual_stats;
 
 int fr_dual_init(fr_ctx* ctx, const void* U, void* stream);
 int fr_dual_step(fr_ctx* ctx, void* U, const fr_dual_opts* opts, fr_dual_stats* stats,
                  void* stream);
 int fr_dual_velocity(const fr_ctx* ctx, double* V, void* stream);
+
+/* Learned initial guess (no counterpart in the paper).  A per-element MLP,
+ * on the tensor cores (BF16 operands, FP32 accumulation, FP32 master
+ * weights), maps the element's last three levels - fed as U^n, the first
+ * and the second difference, each scaled per variable by its RMS - through
+ * two hidden ReLU layers to the correction of the plain extrapolation
+ * 3U^n - 3U^{n-1} + U^{n-2}, scaled per variable by the RMS of the collected
+ * corrections.
+ *   fr_mlp_create   network of `hidden` units per layer bound to ctx, with
+ *                   room for `capacity` element samples; weights drawn from
+ *                   a splitmix64 stream seeded with `seed`.
+ *   fr_mlp_collect  after an fr_dual_step that left four levels in ctx's
+ *                   history: stores `count` element samples (elements drawn
+ *                   from a splitmix64 stream; written to elems if non-NULL)
+ *                   of inputs (the three older levels) and target (the
+ *                   newest).  The first call fixes the input scales.
+ *                   Synchronises `stream`.
+ *   fr_mlp_loss_grad  MSE and its gradients over the collected samples.
+ *   fr_mlp_train    `epochs` full-batch Adam steps (beta 0.9/0.999, eps
+ *                   1e-8, step lr); *loss is the loss before the last step.
+ *   fr_mlp_predict  guess of the next level from ctx's three newest levels:
+ *                   U (context precision) and V (FP64 velocity rows).
+ *   fr_mlp_params   copy to (set = 0) or from (set != 0) host memory:
+ *                   which 0 = parameters, 1 = gradients (count = the total
+ *                   from fr_mlp_info, order W1 b1 W2 b2 W3 b3, W row-major
+ *                   (out x in)); which 2 = scales (3 nv input + nv output);
+ *                   which 3 / 4 (read only) = the collected samples'
+ *                   features (n_in x n_samples, row-major) / raw targets
+ *                   (n_out x n_samples).
+ * Buffers are allocated by fr_mlp_create (and by the first fr_mlp_predict);
+ * FR_EINVAL when the history, samples or training a call needs are missing. */
+int fr_mlp_create(fr_ctx* ctx, int hidden, int capacity, unsigned long long seed, fr_mlp** out);
+void fr_mlp_destroy(fr_mlp* mlp);
+int fr_mlp_info(const fr_mlp* mlp, int* n_in, int* hidden, int* n_out, int* n_samples,
+                size_t* n_params);
+int fr_mlp_collect(fr_mlp* mlp, int count, unsigned long long seed, int* elems, void* stream);
+int fr_mlp_loss_grad(fr_mlp* mlp, double* loss, void* stream);
+int fr_mlp_train(fr_mlp* mlp, int epochs, double lr, double* loss, void* stream);
+int fr_mlp_predict(fr_mlp* mlp, void* U, double* V, void* stream);
+int fr_mlp_params(fr_mlp* mlp, int which, float* host, size_t count, int set);
+
+/* The tensor-core GEMM of the MLP as a utility: C[N x M] = A . B in FP32
+ * from BF16 operands.  amode 0: A[n * lda + k]; 1: A[k * lda + n].
+ * bmode 0: B[k * ldb + m]; 1: B[m * ldb + k].  C[n * ldc + m].  Device
+ * pointers; asynchronous. */
+int fr_gemm_bf16(int amode, int bmode, int N, int M, int K, const void* A, long long lda,
+                 const void* B, long long ldb, float* C, long long ldc, void* stream);
 
 /* Reads the context's device error word after synchronising `stream`;
  * returns FR_ETIMEOUT if a bounded in-kernel wait gave up since the last

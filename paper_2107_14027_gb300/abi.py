@@ -17,12 +17,14 @@ LIB_PATH = os.path.join(HERE, "libacmhd_fr.so")
 FR_OK, FR_EINVAL, FR_ECUDA, FR_ENOCONV, FR_ENONFINITE, FR_ENOMEM, FR_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 FR_F32, FR_F64 = 32, 64
 FR_CORR_DG, FR_CORR_G2 = 0, 1
-FR_GUESS_PREVIOUS, FR_GUESS_EXTRAPOLATE = 0, 1
+FR_GUESS_PREVIOUS, FR_GUESS_EXTRAPOLATE, FR_GUESS_MLP = 0, 1, 2
 
 EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_trace", "fr_rhs_volume",
            "fr_rhs_unfused", "fr_rhs_host",
            "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error", "fr_rhs_static",
-           "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity"]
+           "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity",
+           "fr_mlp_create", "fr_mlp_destroy", "fr_mlp_info", "fr_mlp_collect", "fr_mlp_loss_grad",
+           "fr_mlp_train", "fr_mlp_predict", "fr_mlp_params", "fr_gemm_bf16"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -34,12 +36,13 @@ class fr_dual_opts(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("dtau", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int), ("guess", ctypes.c_int),
                 ("refine", ctypes.c_void_p), ("U_refine", ctypes.c_void_p),
-                ("tol_switch", ctypes.c_double)]
+                ("tol_switch", ctypes.c_double), ("mlp", ctypes.c_void_p)]
 
 
 class fr_dual_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("iters_refine", ctypes.c_int), ("res", ctypes.c_double),
-                ("res_switch", ctypes.c_double)]
+                ("res_switch", ctypes.c_double), ("guess_used", ctypes.c_int),
+                ("res_guess", ctypes.c_double * 2)]
 
 
 class FrError(RuntimeError):
@@ -79,12 +82,24 @@ def _lib():
         lib.fr_dual_step.argtypes = [vp, vp, ctypes.POINTER(fr_dual_opts),
                                      ctypes.POINTER(fr_dual_stats), vp]
         lib.fr_dual_velocity.argtypes = [vp, vp, vp]
+        ull = ctypes.c_ulonglong
+        lib.fr_mlp_create.argtypes = [vp, i32, i32, ull, ctypes.POINTER(vp)]
+        lib.fr_mlp_destroy.argtypes = [vp]
+        lib.fr_mlp_destroy.restype = None
+        lib.fr_mlp_info.argtypes = [vp, ip, ip, ip, ip, ctypes.POINTER(sz)]
+        lib.fr_mlp_collect.argtypes = [vp, i32, ull, ip, vp]
+        lib.fr_mlp_loss_grad.argtypes = [vp, dp, vp]
+        lib.fr_mlp_train.argtypes = [vp, i32, dbl, dp, vp]
+        lib.fr_mlp_predict.argtypes = [vp, vp, vp, vp]
+        lib.fr_mlp_params.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float), sz, i32]
+        lib.fr_gemm_bf16.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.c_longlong, vp,
+                                     ctypes.c_longlong, vp, ctypes.c_longlong, vp]
         lib.fr_strerror.argtypes = [i32]
         lib.fr_strerror.restype = ctypes.c_char_p
         lib.fr_last_error.argtypes = []
         lib.fr_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("fr_destroy", "fr_strerror", "fr_last_error"):
+            if name not in ("fr_destroy", "fr_strerror", "fr_last_error", "fr_mlp_destroy"):
                 getattr(lib, name).restype = i32
         _LIB = lib
     return _LIB
@@ -217,11 +232,12 @@ def fr_dual_init(ctx, U, stream=None):
 
 
 def fr_dual_step(ctx, U, dt, dtau, tol, max_iter, check_every=1, guess=FR_GUESS_EXTRAPOLATE,
-                 refine=None, U_refine=None, tol_switch=0.0, stream=None, allow_noconv=False):
+                 refine=None, U_refine=None, tol_switch=0.0, mlp=None, stream=None,
+                 allow_noconv=False):
     """Returns (status, fr_dual_stats)."""
     opts = fr_dual_opts(float(dt), float(dtau), float(tol), int(max_iter), int(check_every),
                         int(guess), refine, U_refine.data_ptr() if U_refine is not None else None,
-                        float(tol_switch))
+                        float(tol_switch), mlp)
     stats = fr_dual_stats()
     st = _lib().fr_dual_step(ctypes.c_void_p(ctx), _ptr(U), ctypes.byref(opts),
                              ctypes.byref(stats), _stream(stream))
@@ -245,6 +261,74 @@ def new_velocity(ctx, dim, order, device="cuda"):
 def velocity_rows(U, dim, npts):
     """The velocity rows of a packed state tensor (a view)."""
     return U[npts:(1 + dim) * npts]
+
+
+def fr_mlp_create(ctx, hidden, capacity, seed):
+    out = ctypes.c_void_p()
+    _check(_lib().fr_mlp_create(ctypes.c_void_p(ctx), int(hidden), int(capacity), int(seed),
+                                ctypes.byref(out)), "fr_mlp_create")
+    return out.value
+
+
+def fr_mlp_destroy(mlp):
+    _lib().fr_mlp_destroy(ctypes.c_void_p(mlp))
+
+
+def fr_mlp_info(mlp):
+    """(n_in, hidden, n_out, n_samples, n_params)"""
+    a, b_, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    e = ctypes.c_size_t()
+    _check(_lib().fr_mlp_info(ctypes.c_void_p(mlp), ctypes.byref(a), ctypes.byref(b_),
+                              ctypes.byref(c), ctypes.byref(d), ctypes.byref(e)), "fr_mlp_info")
+    return a.value, b_.value, c.value, d.value, e.value
+
+
+def fr_mlp_collect(mlp, count, seed, stream=None):
+    """Returns the sampled element indices (numpy int32)."""
+    el = np.zeros(count, dtype=np.int32)
+    _check(_lib().fr_mlp_collect(ctypes.c_void_p(mlp), int(count), int(seed),
+                                 el.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _stream(stream)),
+           "fr_mlp_collect")
+    return el
+
+
+def fr_mlp_loss_grad(mlp, stream=None):
+    loss = ctypes.c_double()
+    _check(_lib().fr_mlp_loss_grad(ctypes.c_void_p(mlp), ctypes.byref(loss), _stream(stream)),
+           "fr_mlp_loss_grad")
+    return loss.value
+
+
+def fr_mlp_train(mlp, epochs, lr, stream=None):
+    loss = ctypes.c_double()
+    _check(_lib().fr_mlp_train(ctypes.c_void_p(mlp), int(epochs), float(lr), ctypes.byref(loss),
+                               _stream(stream)), "fr_mlp_train")
+    return loss.value
+
+
+def fr_mlp_predict(mlp, U, V, stream=None):
+    _check(_lib().fr_mlp_predict(ctypes.c_void_p(mlp), _ptr(U), _ptr(V), _stream(stream)),
+           "fr_mlp_predict")
+
+
+def fr_mlp_params(mlp, which, values=None, count=None):
+    """Get (values None) or set the parameters (0), gradients (1) or scales (2)."""
+    if values is None:
+        out = np.zeros(int(count), dtype=np.float32)
+        _check(_lib().fr_mlp_params(ctypes.c_void_p(mlp), int(which),
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size, 0),
+               "fr_mlp_params")
+        return out
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    _check(_lib().fr_mlp_params(ctypes.c_void_p(mlp), int(which),
+                                v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), v.size, 1),
+           "fr_mlp_params")
+
+
+def fr_gemm_bf16(amode, bmode, N, M, K, A, lda, B, ldb, C, ldc, stream=None):
+    _check(_lib().fr_gemm_bf16(int(amode), int(bmode), int(N), int(M), int(K), _ptr(A), int(lda),
+                               _ptr(B), int(ldb), _ptr(C), int(ldc), _stream(stream)),
+           "fr_gemm_bf16")
 
 
 def fr_check(ctx, stream=None):

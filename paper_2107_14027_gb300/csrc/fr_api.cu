@@ -106,7 +106,7 @@ int ensure_history(fr_ctx* c) {
   int st;
   if ((st = alloc_zeroed((void**)&c->dual_v, vel_doubles(c) * sizeof(double), "history")) != FR_OK)
     return st;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if ((st = alloc_zeroed(&c->hist_u[i], c->bytes_state, "history")) != FR_OK) return st;
     if ((st = alloc_zeroed((void**)&c->hist_v[i], vel_doubles(c) * sizeof(double), "history")) !=
         FR_OK)
@@ -196,8 +196,9 @@ void fr_destroy(fr_ctx* c) {
   void* bufs[] = {c->trace, c->rk_stage, c->rk_acc, c->rk_k, c->unf_uf, c->unf_f,
                   c->unf_div, c->unf_fi, c->host_u, c->host_r, c->err,
                   c->dual_vs, c->dual_vacc, c->dual_c, c->dual_partial, c->dual_res, c->dual_v,
-                  c->hist_u[0], c->hist_u[1], c->hist_u[2],
-                  c->hist_v[0], c->hist_v[1], c->hist_v[2]};
+                  c->hist_u[0], c->hist_u[1], c->hist_u[2], c->hist_u[3],
+                  c->hist_v[0], c->hist_v[1], c->hist_v[2], c->hist_v[3],
+                  c->guess_u, c->guess_v};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -358,9 +359,39 @@ int fr_dual_init(fr_ctx* c, const void* U, void* stream) {
   return FR_OK;
 }
 
+// Residual of a candidate initial guess (U, V) of the pseudo iteration:
+// one RHS and the velocity RMS of R_tau, as the first RK stage computes it.
+int guess_residual(fr_ctx* c, void* U, double* V, const double* Vn, const double* Vnm1, double dt,
+                   int order, double* res, cudaStream_t s) {
+  int st = ensure_rk(c);
+  if (st == FR_OK) st = ensure_dual(c);
+  if (st != FR_OK) return st;
+  const double a0 = order == 1 ? 1.0 : 1.5, a1 = order == 1 ? -1.0 : -2.0;
+  const double a2 = order == 1 ? 0.0 : 0.5;
+  st = cuda_status(acmhd::launch_bdf_const(c, -a1 / dt, -a2 / dt, Vn, order == 2 ? Vnm1 : Vn,
+                                           c->dual_c, s), "bdf source");
+  if (st == FR_OK) st = cuda_status(acmhd::launch_sync_velocity(c, V, U, s), "velocity sync");
+  if (st == FR_OK) st = fr_rhs(c, U, c->rk_k, s);
+  if (st == FR_OK)
+    st = cuda_status(acmhd::launch_dual_stage(c, 0, 1.0, a0 / dt, U, V, c->dual_c,
+                                              c->dual_partial, s), "guess residual");
+  if (st == FR_OK)
+    st = cuda_status(acmhd::launch_norm_final(c, c->dual_partial,
+                                              (double)c->dim * c->npts * c->ne, c->dual_res, s),
+                     "guess residual");
+  if (st == FR_OK)
+    st = cuda_status(cudaMemcpyAsync(res, c->dual_res, sizeof(double), cudaMemcpyDeviceToHost, s),
+                     "guess residual");
+  if (st == FR_OK) st = cuda_status(cudaStreamSynchronize(s), "stream synchronize");
+  return st;
+}
+
 int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, void* stream) {
   if (!c || bad_state_ptr(U) || !o || c->hist_levels < 1) return FR_EINVAL;
-  if (o->guess != FR_GUESS_PREVIOUS && o->guess != FR_GUESS_EXTRAPOLATE) return FR_EINVAL;
+  if (o->guess != FR_GUESS_PREVIOUS && o->guess != FR_GUESS_EXTRAPOLATE &&
+      o->guess != FR_GUESS_MLP)
+    return FR_EINVAL;
+  if (o->guess == FR_GUESS_MLP && !o->mlp) return FR_EINVAL;
   fr_ctx* rf = o->refine;
   if (rf) {
     // the refinement context must be the FP64 twin of this one
@@ -372,16 +403,18 @@ int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, 
       return FR_EINVAL;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int L = c->hist_levels;
-  const int h0 = c->hist_head, h1 = (h0 + 2) % 3, h2 = (h0 + 1) % 3;  // levels n, n-1, n-2
+  const int L = c->hist_levels < 3 ? c->hist_levels : 3;  // levels used by the guess
+  const int h0 = c->hist_head;
+  const int h1 = acmhd::hist_slot(h0, 1), h2 = acmhd::hist_slot(h0, 2);  // n, n-1, n-2
   const size_t n = (size_t)c->nv * c->npts * c->stride;
   const size_t nv = vel_doubles(c);
   // initial guess of the new level: the previous level, or the polynomial
   // extrapolation through the stored levels (linear with two, quadratic with
   // three: 3 U^n - 3 U^{n-1} + U^{n-2})
+  const bool extrap = o->guess != FR_GUESS_PREVIOUS;
   double w0 = 1.0, w1 = 0.0, w2 = 0.0;
-  if (o->guess == FR_GUESS_EXTRAPOLATE && L == 2) w0 = 2.0, w1 = -1.0;
-  if (o->guess == FR_GUESS_EXTRAPOLATE && L == 3) w0 = 3.0, w1 = -3.0, w2 = 1.0;
+  if (extrap && L == 2) w0 = 2.0, w1 = -1.0;
+  if (extrap && L == 3) w0 = 3.0, w1 = -3.0, w2 = 1.0;
   int st = cuda_status(acmhd::launch_combine3(c, c->precision, n, w0, w1, w2, c->hist_u[h0],
                                               c->hist_u[h1], c->hist_u[h2], U, s),
                        "initial guess");
@@ -391,7 +424,29 @@ int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, 
                      "initial guess");
   if (st != FR_OK) return st;
   const int order = L >= 2 ? 2 : 1;
-  fr_dual_stats stats = {0, 0, NAN, NAN};
+  fr_dual_stats stats = {0, 0, NAN, NAN, extrap ? FR_GUESS_EXTRAPOLATE : FR_GUESS_PREVIOUS,
+                         {NAN, NAN}};
+  if (o->guess == FR_GUESS_MLP && L == 3) {
+    // the network's guess competes with the extrapolation on the residual
+    if ((st = alloc_zeroed(&c->guess_u, c->bytes_state, "guess")) != FR_OK) return st;
+    if ((st = alloc_zeroed((void**)&c->guess_v, nv * sizeof(double), "guess")) != FR_OK) return st;
+    if ((st = fr_mlp_predict(o->mlp, c->guess_u, c->guess_v, stream)) != FR_OK) return st;
+    st = guess_residual(c, U, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
+                        &stats.res_guess[0], s);
+    if (st == FR_OK)
+      st = guess_residual(c, c->guess_u, c->guess_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
+                          &stats.res_guess[1], s);
+    if (st != FR_OK) return st;
+    if (stats.res_guess[1] < stats.res_guess[0]) {
+      stats.guess_used = FR_GUESS_MLP;
+      st = cuda_status(cudaMemcpyAsync(U, c->guess_u, c->bytes_state, cudaMemcpyDeviceToDevice, s),
+                       "guess");
+      if (st == FR_OK)
+        st = cuda_status(cudaMemcpyAsync(c->dual_v, c->guess_v, nv * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, s), "guess");
+      if (st != FR_OK) return st;
+    }
+  }
   // iterations in this context's precision; with a refinement context they
   // stop at tol_switch or when the residual stalls
   const double tol1 = rf ? (o->tol > o->tol_switch ? o->tol : o->tol_switch) : o->tol;
@@ -413,8 +468,8 @@ int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, 
     if (st != FR_OK) return st;
   }
   if (out) *out = stats;
-  // the new level replaces level n-2 in the ring
-  const int hn = (h0 + 1) % 3;
+  // the new level replaces level n-3 in the ring
+  const int hn = (h0 + 1) % 4;
   st = cuda_status(acmhd::launch_combine3(c, c->precision, n, 1.0, 0.0, 0.0, U, nullptr, nullptr,
                                           c->hist_u[hn], s),
                    "history");
@@ -424,7 +479,7 @@ int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, 
                      "history");
   if (st != FR_OK) return st;
   c->hist_head = hn;
-  c->hist_levels = L < 3 ? L + 1 : 3;
+  c->hist_levels = c->hist_levels < 4 ? c->hist_levels + 1 : 4;
   return solve;
 }
 

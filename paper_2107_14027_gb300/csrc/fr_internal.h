@@ -49,6 +49,9 @@ struct FrConst {
   int stride;      // elem_stride
 };
 
+// ring slot of the level `back` steps before the newest one
+inline int hist_slot(int head, int back) { return (head + 4 - back) % 4; }
+
 }  // namespace acmhd
 
 struct fr_ctx {
@@ -84,10 +87,12 @@ struct fr_ctx {
   double* dual_partial;  // residual partial sums (one per block)
   double* dual_res;    // residual (one double)
   double* dual_v;      // velocity master of fr_dual_step
-  void* hist_u[3];     // physical-time levels of the state (precision T)
-  double* hist_v[3];   // physical-time levels of the velocity (FP64)
-  int hist_head;       // slot of level n
-  int hist_levels;     // number of valid levels (0..3)
+  void* hist_u[4];     // physical-time levels of the state (precision T)
+  double* hist_v[4];   // physical-time levels of the velocity (FP64)
+  int hist_head;       // ring slot of the newest level
+  int hist_levels;     // number of valid levels (0..4)
+  void* guess_u;       // alternative initial guess (state, precision T)
+  double* guess_v;     // alternative initial guess (FP64 velocity)
 };
 
 namespace acmhd {
