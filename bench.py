@@ -290,15 +290,22 @@ def run_gpu(args):
     trace_s = _time_loop(lambda: abi.fr_trace(ctx, Ud, stream), stream, K, 2, torch) / K
     fused_s = _time_loop(lambda: abi.fr_rhs_volume(ctx, Ud, Rd, stream), stream, K, 2, torch) / K
 
-    # algorithmic bytes of one fused launch (FP32): read U and the 6 neighbour
-    # face traces of 7 slots, write R
-    alg_bytes = ne * (2 * nv * m ** 3 + 6 * 7 * m ** 2) * 4
+    # algorithmic bytes of one fused launch (FP32).  Byte model of the method
+    # (per element, n_v (2 m^3 + 6 m^2) values: read U and the traces of all
+    # variables on the six faces, write R) and this kernel's own minimum (read
+    # U, write R, read the 7 normal-flux slots on the four y/z faces; x faces
+    # come from neighbouring lanes except at the ends of each 32-element group)
+    alg_bytes = ne * nv * (2 * m ** 3 + 6 * m ** 2) * 4
+    own_bytes = ne * (2 * nv * m ** 3 + 4 * 7 * m ** 2) * 4 + (ne // 32) * 2 * 7 * m ** 2 * 4
     hbm, peak_kind = _peaks()
     achieved = alg_bytes / fused_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": _profiled_traffic(),
                 "kernel": "fused_kernel<3,4,float>", "peak_source": peak_kind,
-                "alg_bytes_per_launch": alg_bytes}
+                "alg_bytes_per_launch": alg_bytes,
+                "own_min_bytes_per_launch": own_bytes,
+                "achieved_own": own_bytes / fused_s / 1e9,
+                "frac_own": own_bytes / fused_s / 1e9 / hbm}
 
     # unfused pipeline and FP64 fused, same stream
     t_unf = _time_loop(lambda: abi.fr_rhs_unfused(ctx, Ud, Rd, stream), stream, K, 2, torch) / K
@@ -372,6 +379,94 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_dual(args):
+    """Dual time stepping on the 3-D p = 4, 48^3 Taylor-Green workload: BDF2
+    physical steps dt = 1e-2, RK4 pseudo steps dtau = 1e-3 to an FP64 velocity
+    residual of 1e-6; FP32 RHS handing over to an FP64 twin at the FP32 floor.
+    Solver A runs the first steps with the plain extrapolated guess while
+    element samples are collected and the network is trained; then a fork B
+    of A (identical history) takes the held-out steps with the learned guess
+    and A with the plain one.  Metric: wall-seconds per held-out physical step
+    (host clock around fr_dual_step, device synchronised)."""
+    import torch
+    from paper_2107_14027_gb300 import abi
+    from paper_2107_14027_gb300 import workloads as W
+    n, order, nv, d = (args.dual_mesh,) * 3, 4, 13, 3
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    zeta, nu, t_r = 2.5, 1.0 / 1600.0, 5e-3
+    dt, dtau, tol, tol_switch = 1e-2, 1e-3, 1e-6, 5e-6
+    n_warm, n_collect, n_held = 3, args.dual_collect_steps, args.dual_held_steps
+    per_step = max(1, args.dual_samples // n_collect)
+    U0 = W.taylor_green(n, lo, hi, order, dtype=np.float32)
+    solvers = []
+    for _ in range(2):
+        c32 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, abi.FR_F32)
+        c64 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, abi.FR_F64)
+        solvers.append([c32, c64, abi.pack_state(c32, U0, abi.FR_F32), abi.new_state(c64, abi.FR_F64)])
+    abi.fr_dual_init(solvers[0][0], solvers[0][2])
+    net = abi.fr_mlp_create(solvers[0][0], 256, per_step * n_collect, seed=2021)
+    log = {"A": [], "B": []}
+
+    def step(k, which, guess, max_iter):
+        c32, c64, U, U64 = solvers[which]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, s = abi.fr_dual_step(c32, U, dt, dtau, tol, max_iter, check_every=5, guess=guess,
+                                 refine=c64, U_refine=U64, tol_switch=tol_switch, mlp=net,
+                                 allow_noconv=True)
+        torch.cuda.synchronize()
+        rec = {"step": k, "wall_s": time.perf_counter() - t0, "iters_fp32": s.iters,
+               "iters_fp64": s.iters_refine, "res": s.res, "res_switch": s.res_switch,
+               "guess": s.guess_used, "res_guess": list(s.res_guess), "converged": st == 0}
+        log["AB"[which]].append(rec)
+        print(json.dumps({"solver": "AB"[which], **rec}), file=sys.stderr, flush=True)
+
+    k = 0
+    for _ in range(n_warm + n_collect):
+        k += 1
+        step(k, 0, abi.FR_GUESS_EXTRAPOLATE, args.dual_train_iters)
+        if k > n_warm:
+            abi.fr_mlp_collect(net, per_step, seed=1000 + k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss0 = abi.fr_mlp_train(net, 1, 1e-3)
+    loss = abi.fr_mlp_train(net, args.dual_epochs - 1, 1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    abi.fr_dual_copy(solvers[1][0], solvers[0][0])
+    for _ in range(n_held):
+        k += 1
+        step(k, 0, abi.FR_GUESS_EXTRAPOLATE, args.dual_held_iters)
+        step(k, 1, abi.FR_GUESS_MLP, args.dual_held_iters)
+    wa = float(np.mean([r["wall_s"] for r in log["A"][-n_held:]]))
+    wb = float(np.mean([r["wall_s"] for r in log["B"]]))
+    Va = abi.new_velocity(solvers[0][0], d, order)
+    Vb = abi.new_velocity(solvers[1][0], d, order)
+    abi.fr_dual_velocity(solvers[0][0], Va)
+    abi.fr_dual_velocity(solvers[1][0], Vb)
+    dv = float((Va - Vb).abs().max().item())
+    out = {
+        "metric": "wall-s per physical step at 1e-6 residual", "value": wb, "unit": "s",
+        "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"hex_p4_{args.dual_mesh}cube_dual", "order": order,
+                   "mesh": list(n), "dt": dt, "dtau": dtau, "tol": tol,
+                   "tol_switch": tol_switch, "bdf": 2, "pseudo": "RK4",
+                   "max_iter_train_steps": args.dual_train_iters,
+                   "max_iter_held_steps": args.dual_held_iters,
+                   "mlp": {"hidden": 256, "samples": per_step * n_collect,
+                           "epochs": args.dual_epochs, "lr": 1e-3, "train_s": t_train,
+                           "loss_first": loss0, "loss_last": loss}},
+        "plain_wall_s": wa, "learned_wall_s": wb, "speedup": wa / wb,
+        "held_out_steps": n_held, "max_velocity_difference": dv,
+        "steps": {"plain": log["A"], "learned": log["B"]},
+    }
+    print(json.dumps(out))
+    for c32, c64, _, _ in solvers:
+        abi.fr_destroy(c32)
+        abi.fr_destroy(c64)
+    abi.fr_mlp_destroy(net)
+
+
 def run_profile_case(args):
     """A smaller copy of the workload (N^3 elements, same order and
     variables) for ncu captures: warm-up + steps fused RHS calls only."""
@@ -402,6 +497,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mesh", type=int, default=None,
                     help="profiling only: run fr_rhs on an N^3 mesh and print its timing")
+    ap.add_argument("--workload", default="rhs", choices=["rhs", "dual"],
+                    help="rhs: the fused RHS (default); dual: BDF2 dual time stepping, "
+                         "plain vs learned initial guess")
+    ap.add_argument("--dual-mesh", type=int, default=48)
+    ap.add_argument("--dual-collect-steps", type=int, default=8)
+    ap.add_argument("--dual-held-steps", type=int, default=5)
+    ap.add_argument("--dual-samples", type=int, default=5000)
+    ap.add_argument("--dual-epochs", type=int, default=400)
+    ap.add_argument("--dual-train-iters", type=int, default=200,
+                    help="pseudo-iteration cap of the steps before the held-out ones")
+    ap.add_argument("--dual-held-iters", type=int, default=600,
+                    help="pseudo-iteration cap of the held-out steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -409,6 +516,8 @@ def main():
         run_reference(args)
     elif args.mesh is not None:
         run_profile_case(args)
+    elif args.workload == "dual":
+        run_dual(args)
     else:
         run_gpu(args)
 

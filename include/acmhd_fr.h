@@ -242,6 +242,11 @@ int fr_dual_step(fr_ctx* ctx, void* U, const fr_dual_opts* opts, fr_dual_stats* 
                  void* stream);
 int fr_dual_velocity(const fr_ctx* ctx, double* V, void* stream);
 
+/* Copies the physical-time history (all stored levels) of src into dst, a
+ * context on the same mesh, order and precision: dst continues from exactly
+ * src's state ("forks" the solver).  Allocates dst's history on first use. */
+int fr_dual_copy(fr_ctx* dst, const fr_ctx* src, void* stream);
+
 /* Learned initial guess (no counterpart in the paper).  A per-element MLP,
  * on the tensor cores (BF16 operands, FP32 accumulation, FP32 master
  * weights), maps the element's last three levels - fed as U^n, the first

@@ -22,7 +22,7 @@ FR_GUESS_PREVIOUS, FR_GUESS_EXTRAPOLATE, FR_GUESS_MLP = 0, 1, 2
 EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_trace", "fr_rhs_volume",
            "fr_rhs_unfused", "fr_rhs_host",
            "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error", "fr_rhs_static",
-           "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity",
+           "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity", "fr_dual_copy",
            "fr_mlp_create", "fr_mlp_destroy", "fr_mlp_info", "fr_mlp_collect", "fr_mlp_loss_grad",
            "fr_mlp_train", "fr_mlp_predict", "fr_mlp_params", "fr_gemm_bf16"]
 
@@ -82,6 +82,7 @@ def _lib():
         lib.fr_dual_step.argtypes = [vp, vp, ctypes.POINTER(fr_dual_opts),
                                      ctypes.POINTER(fr_dual_stats), vp]
         lib.fr_dual_velocity.argtypes = [vp, vp, vp]
+        lib.fr_dual_copy.argtypes = [vp, vp, vp]
         ull = ctypes.c_ulonglong
         lib.fr_mlp_create.argtypes = [vp, i32, i32, ull, ctypes.POINTER(vp)]
         lib.fr_mlp_destroy.argtypes = [vp]
@@ -244,6 +245,11 @@ def fr_dual_step(ctx, U, dt, dtau, tol, max_iter, check_every=1, guess=FR_GUESS_
     if not (st == FR_OK or (allow_noconv and st == FR_ENOCONV)):
         _check(st, "fr_dual_step")
     return st, stats
+
+
+def fr_dual_copy(dst, src, stream=None):
+    _check(_lib().fr_dual_copy(ctypes.c_void_p(dst), ctypes.c_void_p(src), _stream(stream)),
+           "fr_dual_copy")
 
 
 def fr_dual_velocity(ctx, V, stream=None):

@@ -483,6 +483,28 @@ int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, 
   return solve;
 }
 
+int fr_dual_copy(fr_ctx* dst, const fr_ctx* src, void* stream) {
+  if (!dst || !src || dst == src || src->hist_levels < 1 || dst->precision != src->precision ||
+      dst->dim != src->dim || dst->order != src->order || dst->ne != src->ne ||
+      dst->stride != src->stride)
+    return FR_EINVAL;
+  int st = ensure_history(dst);
+  if (st != FR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < 4 && st == FR_OK; ++i) {
+    st = cuda_status(cudaMemcpyAsync(dst->hist_u[i], src->hist_u[i], src->bytes_state,
+                                     cudaMemcpyDeviceToDevice, s), "copy history");
+    if (st == FR_OK)
+      st = cuda_status(cudaMemcpyAsync(dst->hist_v[i], src->hist_v[i],
+                                       vel_doubles(src) * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s), "copy history");
+  }
+  if (st != FR_OK) return st;
+  dst->hist_head = src->hist_head;
+  dst->hist_levels = src->hist_levels;
+  return FR_OK;
+}
+
 int fr_dual_velocity(const fr_ctx* c, double* V, void* stream) {
   if (!c || bad_state_ptr(V) || c->hist_levels < 1) return FR_EINVAL;
   return cuda_status(cudaMemcpyAsync(V, c->hist_v[c->hist_head], vel_doubles(c) * sizeof(double),
