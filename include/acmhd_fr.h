@@ -78,6 +78,7 @@ enum { FR_GUESS_PREVIOUS = 0, FR_GUESS_EXTRAPOLATE = 1, FR_GUESS_MLP = 2 };  /* 
 
 typedef struct fr_mlp fr_mlp;
 enum { FR_CORR_DG = 0, FR_CORR_G2 = 1 };     /* correction function (Sec. 2.1) */
+enum { FR_SCHEDULE_AUTO = 0, FR_SCHEDULE_TWO_KERNELS = 1, FR_SCHEDULE_SWEEP = 2 };
 
 /* Create a context.
  *   order       p, 1..6 (m = p + 1 solution points per direction)
@@ -102,14 +103,29 @@ void fr_destroy(fr_ctx* ctx);
 int fr_layout(const fr_ctx* ctx, size_t* elem_stride, size_t* n_elem,
               size_t* bytes_per_state);
 
-/* Fused right-hand side R = -div F(U) + S(U) (Table fr_adv stages 1-6).
- * Two kernels: a face-trace kernel (stage 1, only the 1 + 2d variables the
- * normal flux needs) and one fused kernel that evaluates the flux (stage 2),
- * the partially corrected divergence (3), the Rusanov/mean common flux (4),
- * the correction (5) and negation plus source (6) per element.
+/* Fused right-hand side R = -div F(U) + S(U) (Table fr_adv stages 1-6):
+ * stage 1 stores face traces (only the 1 + 2d variables the normal flux
+ * needs); the volume work evaluates the flux (stage 2), the partially
+ * corrected divergence (3), the Rusanov/mean common flux (4), the
+ * correction (5) and negation plus source (6) per element.
+ * Schedules (fr_set_schedule): FR_SCHEDULE_TWO_KERNELS runs a trace kernel
+ * and a volume kernel; FR_SCHEDULE_SWEEP runs one persistent kernel that
+ * interleaves both per tile of elements, one element layer (z-plane in 3-D,
+ * x-row in 2-D) apart, so that U and the traces are reused from L2.  The
+ * sweep needs element layers made of whole tiles and at least three layers.
+ * On GB300 the in-flight working set of the sweep (about 456 tiles of
+ * 32 elements) already fills the 129 MB L2, so it measures no faster than
+ * two kernels; FR_SCHEDULE_AUTO (default) runs two kernels.  The sweep's
+ * dependency waits are bounded (1 s): a timeout sets the error word read by
+ * fr_check.
  * U, R: device state buffers (must not alias).  Uses the context's trace
- * scratch.  Asynchronous on `stream`. */
+ * scratch (and, for the sweep, a work queue allocated on first use).
+ * Asynchronous on `stream`. */
 int fr_rhs(fr_ctx* ctx, const void* U, void* R, void* stream);
+
+/* Selects fr_rhs's schedule; FR_EINVAL for FR_SCHEDULE_SWEEP when the mesh
+ * does not admit it. */
+int fr_set_schedule(fr_ctx* ctx, int schedule);
 
 /* The two halves of fr_rhs, for callers that time or schedule them apart.
  * fr_trace: stage 1 only - interpolates U to the faces of every element

@@ -18,8 +18,10 @@ FR_OK, FR_EINVAL, FR_ECUDA, FR_ENOCONV, FR_ENONFINITE, FR_ENOMEM, FR_ETIMEOUT = 
 FR_F32, FR_F64 = 32, 64
 FR_CORR_DG, FR_CORR_G2 = 0, 1
 FR_GUESS_PREVIOUS, FR_GUESS_EXTRAPOLATE, FR_GUESS_MLP = 0, 1, 2
+FR_SCHEDULE_AUTO, FR_SCHEDULE_TWO_KERNELS, FR_SCHEDULE_SWEEP = 0, 1, 2
 
-EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_trace", "fr_rhs_volume",
+EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", "fr_trace",
+           "fr_rhs_volume",
            "fr_rhs_unfused", "fr_rhs_host",
            "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error", "fr_rhs_static",
            "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity", "fr_dual_copy",
@@ -71,6 +73,7 @@ def _lib():
         for name in ("fr_rhs", "fr_rhs_volume", "fr_rhs_unfused", "fr_rhs_host"):
             getattr(lib, name).argtypes = [vp, vp, vp, vp]
         lib.fr_trace.argtypes = [vp, vp, vp]
+        lib.fr_set_schedule.argtypes = [vp, i32]
         lib.fr_rk_step.argtypes = [vp, vp, dbl, vp]
         lib.fr_rhs_static.argtypes = [ctypes.POINTER(fr_mesh), i32, i32, dbl, dbl, dbl, i32, i32,
                                       vp, vp, vp]
@@ -168,6 +171,10 @@ def fr_layout(ctx):
 
 def fr_rhs(ctx, U, R, stream=None):
     _check(_lib().fr_rhs(ctypes.c_void_p(ctx), _ptr(U), _ptr(R), _stream(stream)), "fr_rhs")
+
+
+def fr_set_schedule(ctx, schedule):
+    _check(_lib().fr_set_schedule(ctypes.c_void_p(ctx), int(schedule)), "fr_set_schedule")
 
 
 def fr_trace(ctx, U, stream=None):

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "fr_internal.h"
 
@@ -87,6 +88,54 @@ int ensure_unfused(fr_ctx* c) {
 }
 
 bool bad_state_ptr(const void* p) { return p == nullptr || !aligned16(p); }
+
+// The layer sweep needs whole tiles per element layer (a z-plane in 3-D, an
+// x-row in 2-D) and at least three layers.
+void plan_sweep_shape(fr_ctx* c) {
+  const int E = acmhd::fused_tile_elements(c->dim, c->m, c->precision);
+  const long long L = c->dim == 3 ? (long long)c->mesh.n[0] * c->mesh.n[1] : c->mesh.n[0];
+  c->sweep_ok = 0;
+  if (E <= 0 || L % E != 0 || c->ne % E != 0) return;
+  const long long ntiles = c->ne / E, K = L / E;
+  if (ntiles < 2 * K + 1 || ntiles >= (1LL << 29)) return;
+  c->sweep.ntiles = (int)ntiles;
+  c->sweep.K = (int)K;
+  c->sweep_ok = 1;
+}
+
+// Extra distance (in tiles) between a volume unit and the newest trace unit
+// it depends on, so that the trace is usually finished when it is needed:
+// about the number of CTAs resident at once (152 SMs x 3).  Measured on the
+// 64^3 p=3 workload: no extra lag 1.015 ms per RHS (volume units wait on
+// traces claimed just before them), 456 tiles 0.805 ms, all traces first
+// 0.812 ms, the two-kernel schedule 0.80 ms.
+constexpr int kSweepExtraLag = 456;
+
+// Queue: the trace units of the last K tiles; then for i = 0 .. ntiles-1 the
+// trace unit of tile i (unless already queued) followed by the volume unit of
+// tile i - K; then the volume units of the last K tiles.  Every volume unit
+// of tile t comes after the trace units of tiles t-K .. t+K (periodic).
+int ensure_sweep(fr_ctx* c) {
+  if (c->sweep.units) return FR_OK;
+  const int nt = c->sweep.ntiles, K = c->sweep.K;
+  std::vector<int> u;
+  u.reserve(2 * (size_t)nt);
+  for (int t = nt - K; t < nt; ++t) u.push_back(t);
+  const int lag = K + kSweepExtraLag < nt ? K + kSweepExtraLag : nt;
+  for (int i = 0; i < nt; ++i) {
+    if (i < nt - K) u.push_back(i);
+    if (i >= lag) u.push_back((i - lag) | acmhd::kSweepVolume);
+  }
+  for (int t = nt - lag; t < nt; ++t) u.push_back(t | acmhd::kSweepVolume);
+  int st = alloc_zeroed((void**)&c->sweep.units, u.size() * sizeof(int), "sweep plan");
+  if (st == FR_OK) st = alloc_zeroed((void**)&c->sweep.flags, nt * sizeof(unsigned), "sweep plan");
+  if (st == FR_OK) st = alloc_zeroed((void**)&c->sweep.queue, sizeof(unsigned), "sweep plan");
+  if (st == FR_OK)
+    st = cuda_status(cudaMemcpy(c->sweep.units, u.data(), u.size() * sizeof(int),
+                                cudaMemcpyHostToDevice), "sweep plan");
+  c->sweep.nunits = (int)u.size();
+  return st;
+}
 
 size_t vel_doubles(const fr_ctx* c) { return (size_t)c->dim * c->npts * c->stride; }
 
@@ -174,6 +223,7 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
   }
   fill_const<float>(c, &c->cf);
   fill_const<double>(c, &c->cd);
+  plan_sweep_shape(c);
 
   int st = cuda_status(cudaGetDevice(&c->device), "cudaGetDevice");
   if (st == FR_OK) {
@@ -198,7 +248,7 @@ void fr_destroy(fr_ctx* c) {
                   c->dual_vs, c->dual_vacc, c->dual_c, c->dual_partial, c->dual_res, c->dual_v,
                   c->hist_u[0], c->hist_u[1], c->hist_u[2], c->hist_u[3],
                   c->hist_v[0], c->hist_v[1], c->hist_v[2], c->hist_v[3],
-                  c->guess_u, c->guess_v};
+                  c->guess_u, c->guess_v, c->sweep.units, c->sweep.flags, c->sweep.queue};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -215,9 +265,27 @@ int fr_layout(const fr_ctx* c, size_t* elem_stride, size_t* n_elem, size_t* byte
 int fr_rhs(fr_ctx* c, const void* U, void* R, void* stream) {
   if (!c || bad_state_ptr(U) || bad_state_ptr(R) || U == R) return FR_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c->schedule == FR_SCHEDULE_SWEEP && c->sweep_ok) {
+    int st = ensure_sweep(c);
+    if (st != FR_OK) return st;
+    ++c->sweep_epoch;
+    if (c->sweep_epoch == 0) ++c->sweep_epoch;  // flags start at 0
+    return cuda_status(acmhd::launch_sweep(c, U, c->trace, R, c->sweep, c->sweep_epoch, s),
+                       "sweep kernel");
+  }
   int st = cuda_status(acmhd::launch_trace(c, U, c->trace, s), "trace kernel");
   if (st != FR_OK) return st;
   return cuda_status(acmhd::launch_fused(c, U, c->trace, R, s), "fused kernel");
+}
+
+int fr_set_schedule(fr_ctx* c, int schedule) {
+  if (!c) return FR_EINVAL;
+  if (schedule != FR_SCHEDULE_AUTO && schedule != FR_SCHEDULE_TWO_KERNELS &&
+      schedule != FR_SCHEDULE_SWEEP)
+    return FR_EINVAL;
+  if (schedule == FR_SCHEDULE_SWEEP && !c->sweep_ok) return FR_EINVAL;
+  c->schedule = schedule;
+  return FR_OK;
 }
 
 int fr_trace(fr_ctx* c, const void* U, void* stream) {

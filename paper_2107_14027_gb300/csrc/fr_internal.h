@@ -52,6 +52,18 @@ struct FrConst {
 // ring slot of the level `back` steps before the newest one
 inline int hist_slot(int head, int back) { return (head + 4 - back) % 4; }
 
+// Work queue of the layer sweep (device pointers): `units` lists tile
+// indices, trace units plain and volume units with kSweepVolume set.
+constexpr int kSweepVolume = 1 << 30;
+struct SweepPlan {
+  int* units;
+  int nunits;
+  unsigned* flags;   // per tile: epoch of its last finished trace unit
+  int ntiles;
+  int K;             // tiles per element layer: volume(t) needs trace(t-K .. t+K)
+  unsigned* queue;   // next unit to claim
+};
+
 }  // namespace acmhd
 
 struct fr_ctx {
@@ -93,6 +105,10 @@ struct fr_ctx {
   int hist_levels;     // number of valid levels (0..4)
   void* guess_u;       // alternative initial guess (state, precision T)
   double* guess_v;     // alternative initial guess (FP64 velocity)
+  int schedule;        // FR_SCHEDULE_* requested for fr_rhs
+  int sweep_ok;        // the mesh admits the layer sweep
+  acmhd::SweepPlan sweep;
+  unsigned sweep_epoch;
 };
 
 namespace acmhd {
@@ -102,6 +118,9 @@ cudaError_t launch_trace(const fr_ctx* c, const void* U, void* trace, cudaStream
 cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* trace, void* R,
                          cudaStream_t s);
 cudaError_t launch_unfused(const fr_ctx* c, const void* U, void* R, cudaStream_t s);
+cudaError_t launch_sweep(const fr_ctx* c, const void* U, void* Tr, void* R, const SweepPlan& p,
+                         unsigned epoch, cudaStream_t s);
+int fused_tile_elements(int dim, int m, int precision);
 int dual_norm_blocks(const fr_ctx* c);
 cudaError_t launch_sync_velocity(const fr_ctx* c, const double* V, void* U, cudaStream_t s);
 cudaError_t launch_widen_velocity(const fr_ctx* c, const void* U, double* V, cudaStream_t s);
