@@ -78,7 +78,12 @@ enum { FR_GUESS_PREVIOUS = 0, FR_GUESS_EXTRAPOLATE = 1, FR_GUESS_MLP = 2 };  /* 
 
 typedef struct fr_mlp fr_mlp;
 enum { FR_CORR_DG = 0, FR_CORR_G2 = 1 };     /* correction function (Sec. 2.1) */
-enum { FR_SCHEDULE_AUTO = 0, FR_SCHEDULE_TWO_KERNELS = 1, FR_SCHEDULE_SWEEP = 2 };
+enum {
+  FR_SCHEDULE_AUTO = 0,
+  FR_SCHEDULE_TWO_KERNELS = 1,
+  FR_SCHEDULE_SWEEP = 2,
+  FR_SCHEDULE_FUSED_STAGE = 3
+};
 
 /* Create a context.
  *   order       p, 1..6 (m = p + 1 solution points per direction)
@@ -123,7 +128,26 @@ int fr_layout(const fr_ctx* ctx, size_t* elem_stride, size_t* n_elem,
  * Asynchronous on `stream`. */
 int fr_rhs(fr_ctx* ctx, const void* U, void* R, void* stream);
 
-/* Selects fr_rhs's schedule; FR_EINVAL for FR_SCHEDULE_SWEEP when the mesh
+/* Selects the schedule of fr_rhs, fr_rk_step and fr_pseudo_solve.
+ *   FR_SCHEDULE_TWO_KERNELS  fr_rhs: trace kernel + volume kernel; a pseudo
+ *                            step adds a separate RK4 update kernel per stage.
+ *   FR_SCHEDULE_SWEEP        fr_rhs: the layer sweep (above); separate update.
+ *   FR_SCHEDULE_FUSED_STAGE  fr_rk_step / fr_pseudo_solve: one trace kernel
+ *                            per call, then each RK4 stage is one kernel: the
+ *                            volume work with the stage combination (and the
+ *                            FP64 velocity rows, BDF source and residual
+ *                            partials of fr_pseudo_solve) in its epilogue,
+ *                            writing the face traces of the stage it leaves
+ *                            behind; R is never stored.  Same arithmetic in
+ *                            the same order as the separate update: identical
+ *                            results.  fr_rhs: two kernels.
+ *   FR_SCHEDULE_AUTO         (default) two kernels for fr_rhs; for the pseudo
+ *                            steps the fused stage at p <= 2, where it is
+ *                            faster on GB300, the separate update at p >= 3,
+ *                            where the volume kernel's occupancy serves the
+ *                            update traffic at lower bandwidth than a
+ *                            streaming kernel.
+ * FR_EINVAL for an unknown schedule, and for FR_SCHEDULE_SWEEP when the mesh
  * does not admit it. */
 int fr_set_schedule(fr_ctx* ctx, int schedule);
 
@@ -151,7 +175,9 @@ int fr_rhs_host(fr_ctx* ctx, const void* U_host, void* R_host, void* stream);
 
 /* One classical RK4 step in pseudo time of dU/dtau = R(U) (Sec. 5, read as
  * RK4 with a fixed step): U <- U + dtau/6 (k1 + 2 k2 + 2 k3 + k4), in place.
- * Uses the context's RK registers.  Asynchronous. */
+ * Uses the context's RK registers (allocated on first use; the fused-stage
+ * schedule of fr_set_schedule adds a second stage buffer and a second trace
+ * buffer).  Asynchronous. */
 int fr_rk_step(fr_ctx* ctx, void* U, double dtau, void* stream);
 
 /* fr_rhs for callers that cannot allocate device memory.  The paper has no

@@ -18,7 +18,7 @@ FR_OK, FR_EINVAL, FR_ECUDA, FR_ENOCONV, FR_ENONFINITE, FR_ENOMEM, FR_ETIMEOUT = 
 FR_F32, FR_F64 = 32, 64
 FR_CORR_DG, FR_CORR_G2 = 0, 1
 FR_GUESS_PREVIOUS, FR_GUESS_EXTRAPOLATE, FR_GUESS_MLP = 0, 1, 2
-FR_SCHEDULE_AUTO, FR_SCHEDULE_TWO_KERNELS, FR_SCHEDULE_SWEEP = 0, 1, 2
+FR_SCHEDULE_AUTO, FR_SCHEDULE_TWO_KERNELS, FR_SCHEDULE_SWEEP, FR_SCHEDULE_FUSED_STAGE = 0, 1, 2, 3
 
 EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", "fr_trace",
            "fr_rhs_volume",

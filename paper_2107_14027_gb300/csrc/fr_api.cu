@@ -75,6 +75,60 @@ int ensure_rk(fr_ctx* c) {
   return alloc_zeroed(&c->rk_k, c->bytes_state, "rk registers");
 }
 
+// Scratch of the fused-stage schedule: a second stage input and a second
+// trace buffer (stage inputs U -> S1 -> S2 -> S1 -> U, traces alternating
+// between the two buffers), and one residual partial per CTA.
+int ensure_stage(fr_ctx* c) {
+  int st = ensure_rk(c);
+  if (st == FR_OK) st = alloc_zeroed(&c->rk_stage2, c->bytes_state, "rk registers");
+  if (st == FR_OK) st = alloc_zeroed(&c->trace2, c->trace_bytes, "trace scratch");
+  if (st == FR_OK)
+    st = alloc_zeroed((void**)&c->stage_partial,
+                      (size_t)acmhd::stage_blocks(c) * sizeof(double), "dual registers");
+  return st;
+}
+
+// Stage `stage` (0..3) of the fused-stage schedule.  Stage 0 reads the traces
+// of U from c->trace; every stage writes the traces of its result to the
+// other buffer, so after stage 3 the traces of the new U are in c->trace.
+int fused_stage(fr_ctx* c, int stage, void* U, acmhd::StageArgs a, cudaStream_t s) {
+  static const int kIn[4] = {0, 1, 2, 1};    // 0 = U, 1 = S1, 2 = S2
+  static const int kNext[4] = {1, 2, 1, 0};
+  void* buf[3] = {U, c->rk_stage, c->rk_stage2};
+  a.U = U;
+  a.next = kNext[stage] ? buf[kNext[stage]] : nullptr;
+  a.acc = c->rk_acc;
+  a.tr = (stage % 2 == 0) ? c->trace2 : c->trace;
+  a.stage = stage;
+  const void* tr_in = (stage % 2 == 0) ? c->trace : c->trace2;
+  return cuda_status(acmhd::launch_stage(c, buf[kIn[stage]], tr_in, a, c->stage_partial, s),
+                     "fused stage");
+}
+
+// Pseudo steps with the update fused into the volume kernel: on request, and
+// by default at p <= 2.  Measured on GB300 (FP32, RK4 steps of 3-D meshes of
+// about 38M points per variable): fused/separate 13.1/15.1 ms at p = 1,
+// 12.7/14.3 at p = 2, 6.05/5.53 at p = 3 (64^3), 6.9/4.9 at p = 4 (48^3).
+bool use_fused_stage(const fr_ctx* c) {
+  return c->schedule == FR_SCHEDULE_FUSED_STAGE ||
+         (c->schedule == FR_SCHEDULE_AUTO && c->order <= 2);
+}
+
+// RK4 stage coefficient (dtau/2, dtau/2, dtau, dtau/6) rounded to the
+// context precision as the separate update kernels round it: computed in T
+// for the plain step, in FP64 and then rounded for the dual step.
+double stage_coef(const fr_ctx* c, int stage, double dtau, bool dual) {
+  if (dual) {
+    const double v = stage == 2 ? dtau : (stage == 3 ? dtau / 6.0 : 0.5 * dtau);
+    return c->precision == FR_F32 ? (double)(float)v : v;
+  }
+  if (c->precision == FR_F32) {
+    const float d = (float)dtau;
+    return (double)(stage == 2 ? d : (stage == 3 ? d / 6.0f : d * 0.5f));
+  }
+  return stage == 2 ? dtau : (stage == 3 ? dtau / 6.0 : dtau * 0.5);
+}
+
 int ensure_unfused(fr_ctx* c) {
   const size_t nl = c->npts / c->m;
   const size_t row = c->stride * c->elem_bytes;
@@ -243,7 +297,8 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
 void fr_destroy(fr_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  void* bufs[] = {c->trace, c->rk_stage, c->rk_acc, c->rk_k, c->unf_uf, c->unf_f,
+  void* bufs[] = {c->trace, c->rk_stage, c->rk_acc, c->rk_k, c->rk_stage2, c->trace2,
+                  c->stage_partial, c->unf_uf, c->unf_f,
                   c->unf_div, c->unf_fi, c->host_u, c->host_r, c->err,
                   c->dual_vs, c->dual_vacc, c->dual_c, c->dual_partial, c->dual_res, c->dual_v,
                   c->hist_u[0], c->hist_u[1], c->hist_u[2], c->hist_u[3],
@@ -281,7 +336,7 @@ int fr_rhs(fr_ctx* c, const void* U, void* R, void* stream) {
 int fr_set_schedule(fr_ctx* c, int schedule) {
   if (!c) return FR_EINVAL;
   if (schedule != FR_SCHEDULE_AUTO && schedule != FR_SCHEDULE_TWO_KERNELS &&
-      schedule != FR_SCHEDULE_SWEEP)
+      schedule != FR_SCHEDULE_SWEEP && schedule != FR_SCHEDULE_FUSED_STAGE)
     return FR_EINVAL;
   if (schedule == FR_SCHEDULE_SWEEP && !c->sweep_ok) return FR_EINVAL;
   c->schedule = schedule;
@@ -330,6 +385,17 @@ int fr_rk_step(fr_ctx* c, void* U, double dtau, void* stream) {
   int st = ensure_rk(c);
   if (st != FR_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (use_fused_stage(c)) {
+    // fused stages: one trace kernel, then the update inside each RHS
+    if ((st = ensure_stage(c)) != FR_OK) return st;
+    st = cuda_status(acmhd::launch_trace(c, U, c->trace, s), "trace kernel");
+    for (int stage = 0; stage < 4 && st == FR_OK; ++stage) {
+      acmhd::StageArgs a = {};
+      a.ct = stage_coef(c, stage, dtau, false);
+      st = fused_stage(c, stage, U, a, s);
+    }
+    return st;
+  }
   for (int stage = 0; stage < 4; ++stage) {
     const void* in = stage == 0 ? U : c->rk_stage;
     if ((st = fr_rhs(c, in, c->rk_k, stream)) != FR_OK) return st;
@@ -362,18 +428,46 @@ int fr_pseudo_solve(fr_ctx* c, void* U, double* V, const double* Vn, const doubl
   if (st == FR_OK) st = cuda_status(acmhd::launch_sync_velocity(c, V, U, s), "velocity sync");
   if (st != FR_OK) return st;
   const double count = (double)c->dim * c->npts * c->ne;
+  // fused stages: the RK4 combination, the FP64 velocity rows and the
+  // residual partials run inside the volume kernel
+  const bool fused = use_fused_stage(c);
+  acmhd::StageArgs sa = {};
+  sa.dual = 1;
+  sa.a0dt = a0 / dt;
+  sa.V = V;
+  sa.Vs = c->dual_vs;
+  sa.Vacc = c->dual_vacc;
+  sa.C = c->dual_c;
+  if (fused) {
+    if ((st = ensure_stage(c)) != FR_OK) return st;
+    st = cuda_status(acmhd::launch_trace(c, U, c->trace, s), "trace kernel");
+    if (st != FR_OK) return st;
+  }
+  auto stage_step = [&](int stage) -> int {
+    if (fused) {
+      acmhd::StageArgs a = sa;
+      a.c = stage == 2 ? dtau : (stage == 3 ? dtau / 6.0 : 0.5 * dtau);
+      a.ct = stage_coef(c, stage, dtau, true);
+      return fused_stage(c, stage, U, a, s);
+    }
+    int r = fr_rhs(c, stage == 0 ? U : c->rk_stage, c->rk_k, stream);
+    if (r != FR_OK) return r;
+    return cuda_status(acmhd::launch_dual_stage(c, stage, dtau, a0 / dt, U, V, c->dual_c,
+                                                c->dual_partial, s),
+                       "dual stage");
+  };
   double last = NAN, prev = INFINITY;
   bool converged = false;
   int it = 0;
   for (;;) {
-    if ((st = fr_rhs(c, U, c->rk_k, stream)) != FR_OK) return st;
-    st = cuda_status(acmhd::launch_dual_stage(c, 0, dtau, a0 / dt, U, V, c->dual_c,
-                                              c->dual_partial, s),
-                     "dual stage");
-    if (st != FR_OK) return st;
+    if ((st = stage_step(0)) != FR_OK) return st;
     if (it % check_every == 0 || it == max_iter) {
-      st = cuda_status(acmhd::launch_norm_final(c, c->dual_partial, count, c->dual_res, s),
-                       "residual norm");
+      st = cuda_status(
+          fused ? acmhd::launch_norm_final(c, c->stage_partial, acmhd::stage_blocks(c), count,
+                                           c->dual_res, s)
+                : acmhd::launch_norm_final(c, c->dual_partial, acmhd::dual_norm_blocks(c), count,
+                                           c->dual_res, s),
+          "residual norm");
       if (st == FR_OK)
         st = cuda_status(cudaMemcpyAsync(&last, c->dual_res, sizeof(double),
                                          cudaMemcpyDeviceToHost, s),
@@ -394,13 +488,8 @@ int fr_pseudo_solve(fr_ctx* c, void* U, double* V, const double* Vn, const doubl
       prev = last;
     }
     if (it == max_iter) break;
-    for (int stage = 1; stage < 4; ++stage) {
-      if ((st = fr_rhs(c, c->rk_stage, c->rk_k, stream)) != FR_OK) return st;
-      st = cuda_status(acmhd::launch_dual_stage(c, stage, dtau, a0 / dt, U, V, c->dual_c,
-                                                c->dual_partial, s),
-                       "dual stage");
-      if (st != FR_OK) return st;
-    }
+    for (int stage = 1; stage < 4; ++stage)
+      if ((st = stage_step(stage)) != FR_OK) return st;
     ++it;
   }
   if (iters) *iters = it;
@@ -444,7 +533,7 @@ int guess_residual(fr_ctx* c, void* U, double* V, const double* Vn, const double
     st = cuda_status(acmhd::launch_dual_stage(c, 0, 1.0, a0 / dt, U, V, c->dual_c,
                                               c->dual_partial, s), "guess residual");
   if (st == FR_OK)
-    st = cuda_status(acmhd::launch_norm_final(c, c->dual_partial,
+    st = cuda_status(acmhd::launch_norm_final(c, c->dual_partial, acmhd::dual_norm_blocks(c),
                                               (double)c->dim * c->npts * c->ne, c->dual_res, s),
                      "guess residual");
   if (st == FR_OK)

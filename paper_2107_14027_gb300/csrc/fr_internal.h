@@ -64,6 +64,24 @@ struct SweepPlan {
   unsigned* queue;   // next unit to claim
 };
 
+// Arguments of one fused RK4 stage (k_fused.cu, StageOut): the stage input
+// is read by the volume work, its result goes to `next` (stages 0..2) or to
+// U (stage 3), and the traces of that result to `tr`.
+struct StageArgs {
+  void* U;
+  void* next;
+  void* acc;
+  void* tr;
+  double ct;          // stage coefficient, already rounded to the precision
+  double c, a0dt;     // FP64 velocity rows (dual)
+  int stage;
+  int dual;
+  double* V;
+  double* Vs;
+  double* Vacc;
+  const double* C;
+};
+
 }  // namespace acmhd
 
 struct fr_ctx {
@@ -85,6 +103,9 @@ struct fr_ctx {
   void* rk_stage;      // RK4 stage input
   void* rk_acc;        // RK4 accumulator
   void* rk_k;          // RK4 stage derivative
+  void* rk_stage2;     // second stage input of the fused-stage schedule
+  void* trace2;        // second trace buffer of the fused-stage schedule
+  double* stage_partial;  // residual partial sums of the fused stage (one per CTA)
   void* unf_uf;        // unfused: traces of all variables [2d][nv][m^(d-1)][stride]
   void* unf_f;         // unfused: flux [d][nv][m^d][stride]
   void* unf_div;       // unfused: divergence [nv][m^d][stride]
@@ -128,8 +149,11 @@ cudaError_t launch_bdf_const(const fr_ctx* c, double c1, double c2, const double
                              const double* Vnm1, double* C, cudaStream_t s);
 cudaError_t launch_dual_stage(const fr_ctx* c, int stage, double dtau, double a0dt, void* U,
                               double* V, const double* C, double* partial, cudaStream_t s);
-cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, double count, double* out,
-                              cudaStream_t s);
+cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, int nparts, double count,
+                              double* out, cudaStream_t s);
+cudaError_t launch_stage(const fr_ctx* c, const void* U, const void* Tr, const StageArgs& a,
+                         double* partial, cudaStream_t s);
+int stage_blocks(const fr_ctx* c);
 cudaError_t launch_convert(const fr_ctx* c, size_t n, int prec_in, const void* x, int prec_out,
                            void* y, cudaStream_t s);
 cudaError_t launch_combine3(const fr_ctx* c, int precision, size_t n, double c0, double c1,

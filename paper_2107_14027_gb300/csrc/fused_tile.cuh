@@ -1,0 +1,333 @@
+// The volume work of the fused right-hand side for one tile of elements,
+// shared by the RHS kernels (k_fused.cu) and the fused RK4 stage kernels
+// (k_stage.cu).
+#pragma once
+
+#include "fr_device.cuh"
+
+namespace acmhd {
+
+// traces are read through L2 only when other CTAs of the same kernel write them
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ld_trace(const T* p) {
+  if (COHERENT) return __ldcg(p);
+  return __ldg(p);
+}
+
+// Output policies of the volume work.  Every entry i of R is produced
+// exactly once and handed over as out.store(i, value, pre), which returns the
+// value of the state that the entry leaves behind; pre holds the operands the
+// policy reads for that entry, loaded ahead of the store (out.load /
+// out.load_in), so that the stores, which the compiler must assume may alias
+// later loads, do not serialise the loads behind them.
+//
+// RhsOut stores R, from the thread that finishes the entry.
+template <typename T>
+struct RhsOut {
+  static constexpr bool kStage = false;
+  struct Pre {};
+  T* __restrict__ R;
+  __device__ __forceinline__ Pre load_in(size_t, T) const { return Pre{}; }
+  __device__ __forceinline__ T store(size_t i, T r, const Pre&) {
+    R[i] = r;
+    return r;
+  }
+};
+
+// StageOut folds one classical RK4 stage into the volume work (Sec. 5,
+// pseudo-time stepping), with the combinations of the separate update
+// kernels, so R itself is never stored:
+//   stage 0: acc  = k;       next = U + dtau/2 k
+//   stage 1: acc += 2 k;     next = U + dtau/2 k
+//   stage 2: acc += 2 k;     next = U + dtau   k
+//   stage 3: U    = U + dtau/6 (acc + k)            (next = U)
+// With `dual`, the velocity rows use the FP64 master of the dual time step,
+// k_V = R_V + C - (a0/dt) V_in, V_in = V (stage 0) or Vs, and stage 0 sums
+// k_V^2 (the residual) into `sq`.  The traces of `next` go to `tr`, the
+// other trace buffer, so the next stage needs no trace kernel.
+// Every entry of U, acc, V, Vs and Vacc is read once, by the thread that
+// then writes it, and by no one after that.
+template <typename T>
+struct StageOut {
+  static constexpr bool kStage = true;
+  T* U;              // RK4 base state: read; written at stage 3
+  T* next;           // next stage input (stages 0..2)
+  T* acc;            // RK4 accumulator
+  T* tr;             // traces of the state this stage leaves behind
+  T ct;              // stage coefficient in T (plain rows)
+  double c, a0dt;    // stage coefficient and a0/dt (velocity rows of `dual`)
+  int stage;
+  int dual;
+  size_t vel0, vel1;  // velocity rows: [vel0, vel1)
+  double* V;         // FP64 velocity: base, stage, accumulator, BDF constant
+  double* Vs;
+  double* Vacc;
+  const double* C;
+  double sq;
+
+  // plain rows (P, auxiliary; velocity without `dual`)
+  struct Pre {
+    T a, u0;
+  };
+  __device__ __forceinline__ Pre load(size_t i) const {
+    Pre p;
+    p.a = (stage == 0) ? T(0) : __ldg(acc + i);
+    p.u0 = __ldg(U + i);
+    return p;
+  }
+  // uin: entry i of the stage input, which is U itself at stage 0
+  __device__ __forceinline__ Pre load_in(size_t i, T uin) const {
+    Pre p;
+    p.a = (stage == 0) ? T(0) : __ldg(acc + i);
+    p.u0 = (stage == 0) ? uin : __ldg(U + i);
+    return p;
+  }
+  __device__ __forceinline__ T store(size_t i, T k, const Pre& p) {
+    if (stage == 3) {
+      const T un = fma(ct, p.a + k, p.u0);
+      U[i] = un;
+      return un;
+    }
+    acc[i] = (stage == 0) ? k : fma(T(2), k, p.a);
+    const T us = fma(ct, k, p.u0);
+    next[i] = us;
+    return us;
+  }
+
+  // velocity rows of `dual` (j = i - vel0)
+  struct PreV {
+    double vin, cc, v, vacc;
+  };
+  __device__ __forceinline__ PreV load_v(size_t j) const {
+    PreV p;
+    p.vin = __ldg((stage == 0) ? V + j : Vs + j);
+    p.cc = __ldg(C + j);
+    p.v = (stage == 0) ? p.vin : __ldg(V + j);
+    p.vacc = (stage == 0) ? 0.0 : __ldg(Vacc + j);
+    return p;
+  }
+  __device__ __forceinline__ T store_v(size_t i, size_t j, T k, const PreV& p) {
+    const double kv = static_cast<double>(k) + fma(-a0dt, p.vin, p.cc);
+    if (stage == 0) sq = fma(kv, kv, sq);
+    if (stage == 3) {
+      const double vn = fma(c, p.vacc + kv, p.v);
+      V[j] = vn;
+      const T un = static_cast<T>(vn);
+      U[i] = un;
+      return un;
+    }
+    Vacc[j] = (stage == 0) ? kv : fma(2.0, kv, p.vacc);
+    const double vs = fma(c, kv, p.v);
+    Vs[j] = vs;
+    const T us = static_cast<T>(vs);
+    next[i] = us;
+    return us;
+  }
+};
+
+// Stages 2-6 for one tile of E elements starting at e0 (a multiple of E).
+// sU, sA: shared memory of (1+D) NP E values each.  Every thread of the CTA
+// must call it (it synchronises the CTA).
+// RhsOut: each entry is stored by the thread that finishes it.
+// StageOut (Out::kStage): an auxiliary entry is handed over by the thread
+// that finishes it, with its operands loaded at the start of its slot, and
+// that thread also writes the traces of the new auxiliary values on the
+// faces of its axis.  The P and V entries stay in sA after the last phase; a
+// pointwise pass over the tile hands them over in batches of coalesced
+// entries, and their traces on all faces are taken from sA.  Traces go to
+// out.tr (layout of the trace kernel, x faces only where the lane exchange
+// cannot serve them).
+template <int D, int M, typename T, int E, int NW, bool COHERENT, class Out>
+__device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __restrict__ Tr,
+                                           Out& out, const FrConst<T>& c, int e0, T* sU,
+                                           T* sA) {
+  constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int el = lane % E, sub = lane / E;
+  const int e = e0 + el;
+  const bool valid = e < c.ne;
+  const size_t S = c.stride;
+
+  // stage P and V of the tile (rows of E contiguous values)
+  for (int idx = tid; idx < (1 + D) * NP * E; idx += NW * 32) {
+    const int row = idx / E, x = idx - row * E;
+    sU[idx] = __ldg(U + (size_t)row * S + e0 + x);
+  }
+  int nb[3][2];
+  neighbours<D>(valid ? e : 0, c.n, nb);
+  __syncthreads();
+
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    // the trip count is uniform across the warp (shuffles need every lane)
+    for (int l0 = warp * SUB; l0 < NL; l0 += NW * SUB) {
+      const bool lvalid = l0 + sub < NL;
+      const int l = lvalid ? l0 + sub : NL - 1;
+      const bool act = valid && lvalid;
+      // slot values along the line
+      T u[NS][M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) {
+        const int pt = line_pt<D, M>(a, l, t);
+#pragma unroll
+        for (int s = 0; s <= D; ++s) u[s][t] = sU[(s * NP + pt) * E + el];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+          u[1 + D + i][t] = __ldg(U + ((size_t)aux_var<D>(i, a) * NP + pt) * S + e);
+      }
+      // neighbour traces: issued right after the line's own loads.  In the
+      // x phase a neighbour inside the lane group is served by a shuffle
+      // below, so only the others are read from memory.
+      const bool lo_mem = (a != 0) || (act && !x_pair_on_chip(nb[0][0], e, E));
+      const bool hi_mem = (a != 0) || (act && !x_pair_on_chip(e, nb[0][1], E));
+      T nb_lo[NS], nb_hi[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        nb_lo[s] = lo_mem ? ld_trace<COHERENT>(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S +
+                                               nb[a][0])
+                          : T(0);
+        nb_hi[s] = hi_mem ? ld_trace<COHERENT>(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S +
+                                               nb[a][1])
+                          : T(0);
+      }
+      // own traces, and the common fluxes at the two faces (stage 4)
+      T own_lo[NS], own_hi[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        own_lo[s] = trace_dot<M>(u[s], c.lm);
+        own_hi[s] = trace_dot<M>(u[s], c.lp);
+      }
+      if (a == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          const T from_left = __shfl_up_sync(0xffffffffu, own_hi[s], 1, E);
+          const T from_right = __shfl_down_sync(0xffffffffu, own_lo[s], 1, E);
+          if (!lo_mem) nb_lo[s] = from_left;
+          if (!hi_mem) nb_hi[s] = from_right;
+        }
+      }
+      T fl[NS], fr[NS];
+      common_flux<D>(nb_lo, own_lo, a, c.zeta, c.nu, c.inv_t, fl);
+      common_flux<D>(own_hi, nb_hi, a, c.zeta, c.nu, c.inv_t, fr);
+      if (!act) continue;
+      // per slot: pointwise flux (stage 2), then divergence + correction +
+      // negation (stages 3, 5, 6) along the line
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        // operands of the auxiliary entries of this slot
+        typename Out::Pre pq[M];
+        if (s > D) {
+#pragma unroll
+          for (int t = 0; t < M; ++t)
+            pq[t] = out.load_in(((size_t)aux_var<D>(s - D - 1, a) * NP + line_pt<D, M>(a, l, t)) *
+                                    S + e,
+                                u[s][t]);
+        }
+        T f[M];
+#pragma unroll
+        for (int t = 0; t < M; ++t) f[t] = point_flux<D>(u, t, s, a, c.zeta, c.nu, c.inv_t);
+        // the new values of an auxiliary slot feed the traces of the face
+        // pair of axis a, accumulated point by point in the order and
+        // rounding of trace_dot
+        T t_lo = T(0), t_hi = T(0);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          T r = fma(c.br[a][i], fr[s], c.bl[a][i] * fl[s]);
+#pragma unroll
+          for (int k = 0; k < M; ++k) r = fma(c.A[a][i][k], f[k], r);
+          const int pt = line_pt<D, M>(a, l, i);
+          T nx = T(0);
+          if (s <= D) {
+            const int idx = (s * NP + pt) * E + el;
+            if (a == 0) {
+              sA[idx] = r;
+            } else if (a < D - 1 || Out::kStage) {
+              sA[idx] += r;
+            } else {
+              out.store(((size_t)s * NP + pt) * S + e, sA[idx] + r, typename Out::Pre{});
+            }
+          } else {
+            // auxiliary equation of slot s: finished here, with its source
+            const int v = aux_var<D>(s - D - 1, a);
+            nx = out.store(((size_t)v * NP + pt) * S + e, fma(-u[s][i], c.inv_t, r),
+                           pq[i]);
+          }
+          if constexpr (Out::kStage) {
+            t_lo = (i == 0) ? rn_mul(nx, c.lm[0]) : rn_fma(nx, c.lm[i], t_lo);
+            t_hi = (i == 0) ? rn_mul(nx, c.lp[0]) : rn_fma(nx, c.lp[i], t_hi);
+          }
+        }
+        if constexpr (Out::kStage) {
+          const bool w_lo = (a != 0) || !x_pair_on_chip(nb[0][0], e, E);
+          const bool w_hi = (a != 0) || !x_pair_on_chip(e, nb[0][1], E);
+          if (s > D && w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * S + e] = t_lo;
+          if (s > D && w_hi) out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e] = t_hi;
+        }
+      }
+    }
+    __syncthreads();  // partial sums complete before the next axis; smem free after the last
+  }
+  if constexpr (Out::kStage) {
+    // P and V rows: R of the whole tile is in sA; hand it over entry by
+    // entry (E consecutive entries of a row are E consecutive elements) and
+    // keep the new state in sA for the traces
+    constexpr int NPE = NP * E, TOT = (1 + D) * NPE, NT = NW * 32;
+    auto gidx = [&](int idx) {
+      const int row = idx / E;
+      return (size_t)row * S + e0 + (idx - row * E);
+    };
+    auto real = [&](int idx, int end) { return idx < end && e0 + idx % E < c.ne; };
+    // plain rows: P, and V unless `dual`; KB entries per thread in flight
+    constexpr int KB = 8;
+    const int pend = out.dual ? NPE : TOT;
+    for (int base = tid; base < pend; base += NT * KB) {
+      typename Out::Pre p[KB];
+#pragma unroll
+      for (int k = 0; k < KB; ++k)
+        if (real(base + k * NT, pend)) p[k] = out.load(gidx(base + k * NT));
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        const int idx = base + k * NT;
+        if (real(idx, pend)) sA[idx] = out.store(gidx(idx), sA[idx], p[k]);
+      }
+    }
+    if (out.dual) {
+      constexpr int KV = 4;
+      for (int base = NPE + tid; base < TOT; base += NT * KV) {
+        typename Out::PreV q[KV];
+#pragma unroll
+        for (int k = 0; k < KV; ++k)
+          if (real(base + k * NT, TOT)) q[k] = out.load_v(gidx(base + k * NT) - out.vel0);
+#pragma unroll
+        for (int k = 0; k < KV; ++k) {
+          const int idx = base + k * NT;
+          if (real(idx, TOT)) {
+            const size_t i = gidx(idx);
+            sA[idx] = out.store_v(i, i - out.vel0, sA[idx], q[k]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // P and V slots of the new state on the faces of every axis, from sA
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const bool w_lo = (a != 0) || !x_pair_on_chip(nb[0][0], e, E);
+      const bool w_hi = (a != 0) || !x_pair_on_chip(e, nb[0][1], E);
+      if (!valid || (!w_lo && !w_hi)) continue;
+      for (int l = warp * SUB + sub; l < NL; l += NW * SUB) {
+#pragma unroll
+        for (int s = 0; s <= D; ++s) {
+          T x[M];
+#pragma unroll
+          for (int t = 0; t < M; ++t) x[t] = sA[(s * NP + line_pt<D, M>(a, l, t)) * E + el];
+          if (w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * S + e] = trace_dot<M>(x, c.lm);
+          if (w_hi)
+            out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e] = trace_dot<M>(x, c.lp);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace acmhd

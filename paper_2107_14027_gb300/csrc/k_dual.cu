@@ -215,9 +215,10 @@ cudaError_t launch_dual_stage(const fr_ctx* c, int stage, double dtau, double a0
                                 : dual_stage_t<double>(c, stage, dtau, a0dt, U, V, C, partial, s);
 }
 
-cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, double count, double* out,
-                              cudaStream_t s) {
-  norm_final_kernel<<<1, kThreads, 0, s>>>(grid_blocks(c), partial, count, out);
+cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, int nparts, double count,
+                              double* out, cudaStream_t s) {
+  (void)c;
+  norm_final_kernel<<<1, kThreads, 0, s>>>(nparts, partial, count, out);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@
 // volume unit needs them.  A volume unit waits (bounded) on per-tile flags
 // of the trace units it depends on; those units precede it in the queue and
 // never wait, so the schedule cannot deadlock.
-#include "fr_device.cuh"
+#include "fused_tile.cuh"
 
 namespace acmhd {
 
@@ -56,12 +56,6 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 }
 
 // traces are read through L2 only when other CTAs of the same kernel write them
-template <bool COHERENT, typename T>
-__device__ __forceinline__ T ld_trace(const T* p) {
-  if (COHERENT) return __ldcg(p);
-  return __ldg(p);
-}
-
 }  // namespace
 
 // Stage 1 for one tile of E elements, with the lane layout of the volume
@@ -102,116 +96,6 @@ __device__ __forceinline__ void trace_tile(const T* __restrict__ U, T* __restric
   }
 }
 
-// Stages 2-6 for one tile of E elements starting at e0 (a multiple of E).
-// sU, sA: shared memory of (1+D) NP E values each.  Every thread of the CTA
-// must call it (it synchronises the CTA).
-template <int D, int M, typename T, int E, int NW, bool COHERENT>
-__device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __restrict__ Tr,
-                                           T* __restrict__ R, const FrConst<T>& c, int e0,
-                                           T* sU, T* sA) {
-  constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int el = lane % E, sub = lane / E;
-  const int e = e0 + el;
-  const bool valid = e < c.ne;
-  const size_t S = c.stride;
-
-  // stage P and V of the tile (rows of E contiguous values)
-  for (int idx = tid; idx < (1 + D) * NP * E; idx += NW * 32) {
-    const int row = idx / E, x = idx - row * E;
-    sU[idx] = __ldg(U + (size_t)row * S + e0 + x);
-  }
-  int nb[3][2];
-  neighbours<D>(valid ? e : 0, c.n, nb);
-  __syncthreads();
-
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    // the trip count is uniform across the warp (shuffles need every lane)
-    for (int l0 = warp * SUB; l0 < NL; l0 += NW * SUB) {
-      const bool lvalid = l0 + sub < NL;
-      const int l = lvalid ? l0 + sub : NL - 1;
-      const bool act = valid && lvalid;
-      // slot values along the line
-      T u[NS][M];
-#pragma unroll
-      for (int t = 0; t < M; ++t) {
-        const int pt = line_pt<D, M>(a, l, t);
-#pragma unroll
-        for (int s = 0; s <= D; ++s) u[s][t] = sU[(s * NP + pt) * E + el];
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-          u[1 + D + i][t] = __ldg(U + ((size_t)aux_var<D>(i, a) * NP + pt) * S + e);
-      }
-      // neighbour traces: issued right after the line's own loads.  In the
-      // x phase a neighbour inside the lane group is served by a shuffle
-      // below, so only the others are read from memory.
-      const bool lo_mem = (a != 0) || (act && !x_pair_on_chip(nb[0][0], e, E));
-      const bool hi_mem = (a != 0) || (act && !x_pair_on_chip(e, nb[0][1], E));
-      T nb_lo[NS], nb_hi[NS];
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        nb_lo[s] = lo_mem ? ld_trace<COHERENT>(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S +
-                                               nb[a][0])
-                          : T(0);
-        nb_hi[s] = hi_mem ? ld_trace<COHERENT>(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S +
-                                               nb[a][1])
-                          : T(0);
-      }
-      // own traces, and the common fluxes at the two faces (stage 4)
-      T own_lo[NS], own_hi[NS];
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        own_lo[s] = trace_dot<M>(u[s], c.lm);
-        own_hi[s] = trace_dot<M>(u[s], c.lp);
-      }
-      if (a == 0) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          const T from_left = __shfl_up_sync(0xffffffffu, own_hi[s], 1, E);
-          const T from_right = __shfl_down_sync(0xffffffffu, own_lo[s], 1, E);
-          if (!lo_mem) nb_lo[s] = from_left;
-          if (!hi_mem) nb_hi[s] = from_right;
-        }
-      }
-      T fl[NS], fr[NS];
-      common_flux<D>(nb_lo, own_lo, a, c.zeta, c.nu, c.inv_t, fl);
-      common_flux<D>(own_hi, nb_hi, a, c.zeta, c.nu, c.inv_t, fr);
-      if (!act) continue;
-      // per slot: pointwise flux (stage 2), then divergence + correction +
-      // negation (stages 3, 5, 6) along the line
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        T f[M];
-#pragma unroll
-        for (int t = 0; t < M; ++t) f[t] = point_flux<D>(u, t, s, a, c.zeta, c.nu, c.inv_t);
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-          T r = fma(c.br[a][i], fr[s], c.bl[a][i] * fl[s]);
-#pragma unroll
-          for (int k = 0; k < M; ++k) r = fma(c.A[a][i][k], f[k], r);
-          const int pt = line_pt<D, M>(a, l, i);
-          if (s <= D) {
-            const int idx = (s * NP + pt) * E + el;
-            if (a == 0) {
-              sA[idx] = r;
-            } else if (a < D - 1) {
-              sA[idx] += r;
-            } else {
-              R[((size_t)s * NP + pt) * S + e] = sA[idx] + r;
-            }
-          } else {
-            // auxiliary equation of slot s: finished here, with its source
-            const int v = aux_var<D>(s - D - 1, a);
-            R[((size_t)v * NP + pt) * S + e] = fma(-u[s][i], c.inv_t, r);
-          }
-        }
-      }
-    }
-    __syncthreads();  // partial sums complete before the next axis; smem free after the last
-  }
-}
-
 template <int D, int M, typename T, int E, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB)
 fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ R,
@@ -220,7 +104,8 @@ fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sU = reinterpret_cast<T*>(smem_raw);  // [1+D][NP][E]
   T* sA = sU + (1 + D) * NP * E;           // [1+D][NP][E]
-  fused_tile<D, M, T, E, NW, false>(U, Tr, R, c, blockIdx.x * E, sU, sA);
+  RhsOut<T> out{R};
+  fused_tile<D, M, T, E, NW, false>(U, Tr, out, c, blockIdx.x * E, sU, sA);
 }
 
 template <int D, int M, typename T, int E, int NW, int MINB>
@@ -265,7 +150,8 @@ sweep_kernel(const T* __restrict__ U, T* __restrict__ Tr, T* __restrict__ R, con
       }
       __syncthreads();
       __threadfence();
-      fused_tile<D, M, T, E, NW, true>(U, Tr, R, c, tile * E, sU, sA);
+      RhsOut<T> out{R};
+      fused_tile<D, M, T, E, NW, true>(U, Tr, out, c, tile * E, sU, sA);
     }
   }
 }
