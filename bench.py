@@ -57,7 +57,7 @@ def _peaks():
 
 def _source_digest():
     h = hashlib.sha256()
-    for name in ("k_fused.cu", "fr_device.cuh"):
+    for name in ("k_fused.cu", "fused_tile.cuh", "fr_device.cuh"):
         with open(os.path.join(ROOT, "paper_2107_14027_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
