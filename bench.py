@@ -491,6 +491,55 @@ def run_profile_case(args):
                       "gdof_s": dof * args.steps / t / 1e9}))
 
 
+def run_rk(args):
+    """RK4 pseudo-steps (fr_rk_step) on an N^3 Taylor-Green mesh of order p,
+    FP32: the fused-stage schedule (RK4 combination and next-stage traces in
+    the volume kernel) against the separate trace + volume + update kernels.
+    One pseudo-step is four RHS evaluations."""
+    import torch
+    from paper_2107_14027_gb300 import abi
+    from paper_2107_14027_gb300 import workloads as W
+    order = args.rk_order
+    nside = args.rk_mesh or W.ORDER_SWEEP_MESH[order]
+    n = (nside,) * 3
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    U = W.taylor_green(n, lo, hi, order, dtype=np.float32)
+    ctx = abi.fr_create(n, lo, hi, order, 13, 2.5, 1 / 1600, 5e-3, abi.FR_F32, 0)
+    stride, ne, _ = abi.fr_layout(ctx)
+    stream = torch.cuda.current_stream()
+    dof = ne * (order + 1) ** 3 * 13
+    res, outs = {}, {}
+    for name, sched in (("fused_stage", abi.FR_SCHEDULE_FUSED_STAGE),
+                        ("separate", abi.FR_SCHEDULE_TWO_KERNELS)):
+        abi.fr_set_schedule(ctx, sched)
+        Ud = abi.pack_state(ctx, U, abi.FR_F32)
+        abi.fr_rk_step(ctx, Ud, 1e-4, stream)
+        outs[name] = Ud.clone()
+        for _ in range(args.warmup):
+            abi.fr_rk_step(ctx, Ud, 1e-4, stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            abi.fr_rk_step(ctx, Ud, 1e-4, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        res[name] = {"ms_per_step": ms, "gdof_s": 4 * dof / ms / 1e6}
+    same = bool(torch.equal(outs["fused_stage"][:, :ne], outs["separate"][:, :ne]))
+    abi.fr_destroy(ctx)
+    auto = "fused_stage" if order <= 3 else "separate"
+    print(json.dumps({
+        "metric": "GDOF-RHS/s in RK4 pseudo-steps (4 RHS per step)", "value": res[auto]["gdof_s"],
+        "unit": "GDOF/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"hex_p{order}_{nside}cube_rk4", "order": order, "mesh": list(n),
+                   "auto_schedule": auto},
+        "fused_stage": res["fused_stage"], "separate": res["separate"],
+        "fused_over_separate": res["separate"]["ms_per_step"] / res["fused_stage"]["ms_per_step"],
+        "bitwise_equal_after_one_step": same}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,9 +549,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mesh", type=int, default=None,
                     help="profiling only: run fr_rhs on an N^3 mesh and print its timing")
-    ap.add_argument("--workload", default="rhs", choices=["rhs", "dual"],
+    ap.add_argument("--workload", default="rhs", choices=["rhs", "dual", "rk"],
                     help="rhs: the fused RHS (default); dual: BDF2 dual time stepping, "
-                         "plain vs learned initial guess")
+                         "plain vs learned initial guess; rk: RK4 pseudo-steps, fused "
+                         "stage vs separate update")
+    ap.add_argument("--rk-order", type=int, default=3)
+    ap.add_argument("--rk-mesh", type=int, default=None,
+                    help="elements per direction (default: the order sweep's mesh)")
     ap.add_argument("--dual-mesh", type=int, default=48)
     ap.add_argument("--dual-collect-steps", type=int, default=8)
     ap.add_argument("--dual-held-steps", type=int, default=5)
@@ -523,6 +576,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "dual":
         run_dual(args)
+    elif args.workload == "rk":
+        run_rk(args)
     else:
         run_gpu(args)
 

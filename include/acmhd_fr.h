@@ -142,8 +142,8 @@ int fr_rhs(fr_ctx* ctx, const void* U, void* R, void* stream);
  *                            the same order as the separate update: identical
  *                            results.  fr_rhs: two kernels.
  *   FR_SCHEDULE_AUTO         (default) two kernels for fr_rhs; for the pseudo
- *                            steps the fused stage at p <= 2, where it is
- *                            faster on GB300, the separate update at p >= 3,
+ *                            steps the fused stage at p <= 3, where it is
+ *                            faster on GB300, the separate update at p >= 4,
  *                            where the volume kernel's occupancy serves the
  *                            update traffic at lower bandwidth than a
  *                            streaming kernel.

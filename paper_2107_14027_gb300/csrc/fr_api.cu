@@ -106,12 +106,16 @@ int fused_stage(fr_ctx* c, int stage, void* U, acmhd::StageArgs a, cudaStream_t 
 }
 
 // Pseudo steps with the update fused into the volume kernel: on request, and
-// by default at p <= 2.  Measured on GB300 (FP32, RK4 steps of 3-D meshes of
-// about 38M points per variable): fused/separate 13.1/15.1 ms at p = 1,
-// 12.7/14.3 at p = 2, 6.05/5.53 at p = 3 (64^3), 6.9/4.9 at p = 4 (48^3).
+// by default at p <= 3.  Measured on GB300 (FP32 RK4 steps on the 3-D order
+// sweep meshes of about 38M points per variable, fused / separate):
+// p = 1 12.9 / 15.2 ms, p = 2 12.3 / 14.3, p = 3 11.4 / 12.6, p = 4 17.7 /
+// 13.7, p = 5 18.4 / 14.7, p = 6 23.2 / 17.3.  At p >= 4 the stage kernel's
+// larger line work leaves too few resident warps to stream the update
+// traffic as fast as the separate update kernel does.  FP64 (ALU bound on
+// this part): equal times at p = 1..3.
 bool use_fused_stage(const fr_ctx* c) {
   return c->schedule == FR_SCHEDULE_FUSED_STAGE ||
-         (c->schedule == FR_SCHEDULE_AUTO && c->order <= 2);
+         (c->schedule == FR_SCHEDULE_AUTO && c->order <= 3);
 }
 
 // RK4 stage coefficient (dtau/2, dtau/2, dtau, dtau/6) rounded to the

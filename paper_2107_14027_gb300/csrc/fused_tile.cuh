@@ -82,16 +82,16 @@ struct StageOut {
     p.u0 = (stage == 0) ? uin : __ldg(U + i);
     return p;
   }
+  // One code path for all four stages (selects and a predicated store, the
+  // same operations as the separate update kernels): this is inlined at
+  // every point of every line, and branches per stage would multiply the
+  // kernel's code beyond what the instruction cache holds.
   __device__ __forceinline__ T store(size_t i, T k, const Pre& p) {
-    if (stage == 3) {
-      const T un = fma(ct, p.a + k, p.u0);
-      U[i] = un;
-      return un;
-    }
-    acc[i] = (stage == 0) ? k : fma(T(2), k, p.a);
-    const T us = fma(ct, k, p.u0);
-    next[i] = us;
-    return us;
+    const bool last = (stage == 3);
+    const T un = fma(ct, last ? p.a + k : k, p.u0);
+    if (!last) acc[i] = (stage == 0) ? k : fma(T(2), k, p.a);
+    (last ? U : next)[i] = un;
+    return un;
   }
 
   // velocity rows of `dual` (j = i - vel0)
@@ -107,21 +107,15 @@ struct StageOut {
     return p;
   }
   __device__ __forceinline__ T store_v(size_t i, size_t j, T k, const PreV& p) {
+    const bool last = (stage == 3);
     const double kv = static_cast<double>(k) + fma(-a0dt, p.vin, p.cc);
-    if (stage == 0) sq = fma(kv, kv, sq);
-    if (stage == 3) {
-      const double vn = fma(c, p.vacc + kv, p.v);
-      V[j] = vn;
-      const T un = static_cast<T>(vn);
-      U[i] = un;
-      return un;
-    }
-    Vacc[j] = (stage == 0) ? kv : fma(2.0, kv, p.vacc);
-    const double vs = fma(c, kv, p.v);
-    Vs[j] = vs;
-    const T us = static_cast<T>(vs);
-    next[i] = us;
-    return us;
+    sq = (stage == 0) ? fma(kv, kv, sq) : sq;
+    const double vn = fma(c, last ? p.vacc + kv : kv, p.v);
+    if (!last) Vacc[j] = (stage == 0) ? kv : fma(2.0, kv, p.vacc);
+    (last ? V : Vs)[j] = vn;
+    const T un = static_cast<T>(vn);
+    (last ? U : next)[i] = un;
+    return un;
   }
 };
 
