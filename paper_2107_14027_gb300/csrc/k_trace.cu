@@ -10,18 +10,36 @@
 // interpolates one line of each slot variable to both ends.  x-face traces
 // are stored only for the elements whose x-neighbour will read them from
 // memory (x_pair_on_chip): the fused kernel exchanges the others between
-// lanes.
+// lanes.  P and V are slots of every face, so where they fit in 32 KB the
+// tile's P and V are read from HBM once into shared memory and the axes take
+// them from there (otherwise each axis reads them again through the caches).
 #include "fr_device.cuh"
 
 namespace acmhd {
+
+template <int D, int M, typename T>
+constexpr bool trace_stages_pv() {
+  return size_t(1 + D) * ipow<M>(D) * 32 * sizeof(T) <= 32 * 1024;
+}
 
 template <int D, int M, typename T, int E, int EF>
 __global__ void __launch_bounds__(256)
 trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c) {
   constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
+  constexpr bool PV = trace_stages_pv<D, M, T>();
+  __shared__ T sPV[PV ? (1 + D) * NP * E : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int e = blockIdx.x * E + lane % E;
+  const int el = lane % E;
+  const int e = blockIdx.x * E + el;
   const int sub = lane / E;
+  if constexpr (PV) {
+    // rows of E contiguous elements; the tile lies inside the padded stride
+    for (int idx = threadIdx.x; idx < (1 + D) * NP * E; idx += blockDim.x) {
+      const int row = idx / E, x = idx - row * E;
+      sPV[idx] = __ldg(U + (size_t)row * c.stride + blockIdx.x * E + x);
+    }
+    __syncthreads();
+  }
   if (e >= c.ne) return;
   const size_t S = c.stride;
   int nb[3][2];
@@ -42,8 +60,11 @@ trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c) {
       for (int s = 0; s < NS; ++s) {
         const int v = slot_var<D>(s, a);
 #pragma unroll
-        for (int t = 0; t < M; ++t)
-          x[s][t] = __ldg(U + ((size_t)v * NP + line_pt<D, M>(a, l, t)) * S + e);
+        for (int t = 0; t < M; ++t) {
+          const int pt = line_pt<D, M>(a, l, t);
+          x[s][t] = (PV && s <= D) ? sPV[(s * NP + pt) * E + el]
+                                   : __ldg(U + ((size_t)v * NP + pt) * S + e);
+        }
       }
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
