@@ -491,6 +491,56 @@ def run_profile_case(args):
                       "gdof_s": dof * args.steps / t / 1e9}))
 
 
+def run_sweep(args):
+    """Order sweep p = 1..6 on 3-D Taylor-Green meshes of about 38M points per
+    variable (168^3 .. 48^3; 67^3 at p = 4), 13 variables, FP32: the fused
+    RHS (trace + volume kernel) against the six unfused stage kernels, with
+    each kernel's time and the fused RHS's fraction of the HBM roofline for
+    its own minimum traffic (read U once, write R once, write and read the
+    stored face traces once)."""
+    import torch
+    from paper_2107_14027_gb300 import abi
+    from paper_2107_14027_gb300 import workloads as W
+    peak, peak_src = _peaks()
+    stream = torch.cuda.current_stream()
+    rows = []
+    orders = [int(x) for x in args.sweep_orders.split(",")]
+    for order in orders:
+        nside = W.ORDER_SWEEP_MESH[order]
+        n = (nside,) * 3
+        lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+        U = W.taylor_green(n, lo, hi, order, dtype=np.float32)
+        ctx = abi.fr_create(n, lo, hi, order, 13, 2.5, 1 / 1600, 5e-3, abi.FR_F32, 0)
+        stride, ne, nbytes = abi.fr_layout(ctx)
+        Ud = abi.pack_state(ctx, U, abi.FR_F32)
+        Rd = abi.new_state(ctx, abi.FR_F32)
+        K, Wm = args.steps, args.warmup
+        t_rhs = _time_loop(lambda: abi.fr_rhs(ctx, Ud, Rd, stream), stream, K, Wm, torch) / K
+        t_tr = _time_loop(lambda: abi.fr_trace(ctx, Ud, stream), stream, K, Wm, torch) / K
+        t_vol = _time_loop(lambda: abi.fr_rhs_volume(ctx, Ud, Rd, stream), stream, K, Wm,
+                           torch) / K
+        Ku = max(2, K // 4)
+        t_unf = _time_loop(lambda: abi.fr_rhs_unfused(ctx, Ud, Rd, stream), stream, Ku, 2,
+                           torch) / Ku
+        abi.fr_destroy(ctx)
+        del Ud, Rd
+        torch.cuda.empty_cache()
+        m = order + 1
+        dof = ne * m ** 3 * 13
+        # own minimum of the two-kernel RHS: U read once, R written once, the
+        # y/z face traces (7 slots, 4 faces) written and read once
+        own = ne * (2 * 13 * m ** 3 + 2 * 4 * 7 * m * m) * 4
+        rows.append({"order": order, "mesh": nside, "gdof_s": dof / t_rhs / 1e9,
+                     "unfused_gdof_s": dof / t_unf / 1e9, "fused_speedup": t_unf / t_rhs,
+                     "ms": {"rhs": 1e3 * t_rhs, "trace": 1e3 * t_tr, "volume": 1e3 * t_vol,
+                            "unfused": 1e3 * t_unf},
+                     "own_min_gb": own / 1e9, "hbm_frac_own": own / t_rhs / 1e9 / peak})
+    print(json.dumps({"metric": "GDOF-RHS/s, order sweep, fused vs unfused", "unit": "GDOF/s",
+                      "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "steps": args.steps, "warmup": args.warmup, "peak_gbs": peak,
+                      "peak_source": peak_src, "orders": rows}))
+
+
 def run_rk(args):
     """RK4 pseudo-steps (fr_rk_step) on an N^3 Taylor-Green mesh of order p,
     FP32: the fused-stage schedule (RK4 combination and next-stage traces in
@@ -549,10 +599,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mesh", type=int, default=None,
                     help="profiling only: run fr_rhs on an N^3 mesh and print its timing")
-    ap.add_argument("--workload", default="rhs", choices=["rhs", "dual", "rk"],
+    ap.add_argument("--workload", default="rhs", choices=["rhs", "dual", "rk", "sweep"],
                     help="rhs: the fused RHS (default); dual: BDF2 dual time stepping, "
                          "plain vs learned initial guess; rk: RK4 pseudo-steps, fused "
-                         "stage vs separate update")
+                         "stage vs separate update; sweep: orders 1..6, fused vs unfused")
+    ap.add_argument("--sweep-orders", default="1,2,3,4,5,6")
     ap.add_argument("--rk-order", type=int, default=3)
     ap.add_argument("--rk-mesh", type=int, default=None,
                     help="elements per direction (default: the order sweep's mesh)")
@@ -578,6 +629,8 @@ def main():
         run_dual(args)
     elif args.workload == "rk":
         run_rk(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_gpu(args)
 
