@@ -46,6 +46,38 @@ def _rank_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def _init_dist(backend):
+    """Process group of a torchrun launch (RANK, WORLD_SIZE and MASTER_* from
+    the environment); None for a single process."""
+    _, _, world = _rank_env()
+    if world == 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend)
+    return dist
+
+
+def _max_over_ranks(dist, seconds, device):
+    """The job's time: the slowest rank's (replicas run independently)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / seconds
+
+
+def _reference_runs_here():
+    """The reference arm runs on rank 0 only; other ranks exit without work."""
+    rank, _, world = _rank_env()
+    return world == 1 or rank == 0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -166,8 +198,7 @@ print(json.dumps({{"t": dt, "reps": k, "dof": U.size}}))
 
 
 def run_reference(args):
-    rank, _, world = _rank_env()
-    if world > 1 and rank != 0:
+    if not _reference_runs_here():
         return
     # one oracle RHS on a 12^3-element p = 3 sample of the 64^3 workload per step
     n_side = 12
@@ -227,10 +258,7 @@ def run_gpu(args):
     import torch
     rank, local_rank, world = _rank_env()
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = _init_dist("nccl")
 
     from paper_2107_14027_gb300 import abi
     from paper_2107_14027_gb300 import workloads as W
@@ -275,12 +303,8 @@ def run_gpu(args):
         if args.steps * (t_total / max(args.steps, 1)) < 1.0:
             # keep the sampler alive for a few samples on very short runs
             time.sleep(0.5)
-    t_max = t_total
-    if dist is not None:
-        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * dof * args.steps / t_max / 1e9
+    t_max = _max_over_ranks(dist, t_total, "cuda")
+    value = _job_rate(dof * args.steps, world, t_max) / 1e9
 
     # per-kernel timing on the launching stream: the trace kernel alone
     # (fr_trace) and the fused kernel alone (fr_rhs_volume, reading the
@@ -340,12 +364,8 @@ def run_gpu(args):
         abi.fr_rhs_host(ctx, Uh, Rh, stream)
     barrier()
     te = time.perf_counter() - t0
-    te_max = te
-    if dist is not None:
-        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te_max = float(tt.item())
-    e2e = {"value": world * dof * Ke / te_max / 1e9, "unit": "GDOF/s",
+    te_max = _max_over_ranks(dist, te, "cuda")
+    e2e = {"value": _job_rate(dof * Ke, world, te_max) / 1e9, "unit": "GDOF/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
            "call": "fr_rhs_host"}
     abi.fr_destroy(ctx)
