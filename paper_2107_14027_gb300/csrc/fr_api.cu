@@ -96,7 +96,7 @@ int fused_stage(fr_ctx* c, int stage, void* U, acmhd::StageArgs a, cudaStream_t 
   static const int kNext[4] = {1, 2, 1, 0};
   void* buf[3] = {U, c->rk_stage, c->rk_stage2};
   a.U = U;
-  a.next = kNext[stage] ? buf[kNext[stage]] : nullptr;
+  a.next = buf[kNext[stage]];  // stage 3 stores to U (and never through `next`)
   a.acc = c->rk_acc;
   a.tr = (stage % 2 == 0) ? c->trace2 : c->trace;
   a.stage = stage;

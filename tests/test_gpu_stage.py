@@ -146,3 +146,36 @@ def test_fused_stage_full_size_step_matches_separate_update(abi):
         assert torch.equal(a[:, :ne], b[:, :ne])
     finally:
         abi.fr_destroy(ctx)
+
+
+@pytest.mark.parametrize("n,order,precision", [((32, 2, 8), 3, 32), ((32, 5), 2, 64)])
+def test_pseudo_solve_on_every_schedule_gives_the_same_state(abi, n, order, precision):
+    """Layer sweep + separate update, two kernels + separate update and the
+    fused stage: one state, bit for bit, after fixed iterations."""
+    d = len(n)
+    ctx, U, nv = _ctx(abi, n, order, precision)
+    rng = np.random.default_rng(5)
+    Un = U + 1e-3 * rng.standard_normal(U.shape)
+    try:
+        stride, ne, _ = abi.fr_layout(ctx)
+        out = []
+        for sched in (abi.FR_SCHEDULE_SWEEP, abi.FR_SCHEDULE_TWO_KERNELS,
+                      abi.FR_SCHEDULE_FUSED_STAGE):
+            abi.fr_set_schedule(ctx, sched)
+            Ud = abi.pack_state(ctx, U, precision)
+            V = abi.new_velocity(ctx, d, order)
+            Vn = abi.new_velocity(ctx, d, order)
+            for dst, X in ((V, U), (Vn, Un)):
+                dst[:, :ne] = torch.from_numpy(np.ascontiguousarray(X[1:1 + d]).reshape(-1, ne)).to(
+                    "cuda")
+            st, it, res = abi.fr_pseudo_solve(ctx, Ud, V, Vn, Vn, 1e-2, 2, 1e-3, 0.0, 6,
+                                              check_every=3, allow_noconv=True)
+            assert st == abi.FR_ENOCONV and it == 6
+            out.append((Ud, V))
+        torch.cuda.synchronize()
+        abi.fr_check(ctx)                         # the sweep's bounded waits did not time out
+        for Ux, Vx in out[1:]:
+            assert torch.equal(out[0][0][:, :ne], Ux[:, :ne])
+            assert torch.equal(out[0][1][:, :ne], Vx[:, :ne])
+    finally:
+        abi.fr_destroy(ctx)
