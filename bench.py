@@ -403,7 +403,9 @@ def run_dual(args):
     """Dual time stepping on the 3-D p = 4, 48^3 Taylor-Green workload: BDF2
     physical steps dt = 1e-2, RK4 pseudo steps dtau = 1e-3 to an FP64 velocity
     residual of --dual-tol (1e-6); FP32 RHS, handing over to an FP64 twin at the
-    FP32 floor when the tolerance lies below it.
+    FP32 floor when the tolerance lies below it.  --dual-order, --dual-mesh,
+    --dual-dtau and --dual-precision 64 (FP64 throughout, no twin) select
+    other cases of the same problem.
     Solver A runs the first steps with the plain extrapolated guess while
     element samples are collected and the network is trained; then a fork B
     of A (identical history) takes the held-out steps with the learned guess
@@ -412,21 +414,23 @@ def run_dual(args):
     import torch
     from paper_2107_14027_gb300 import abi
     from paper_2107_14027_gb300 import workloads as W
-    n, order, nv, d = (args.dual_mesh,) * 3, 4, 13, 3
+    n, order, nv, d = (args.dual_mesh,) * 3, args.dual_order, 13, 3
     lo, hi = (-np.pi,) * 3, (np.pi,) * 3
     zeta, nu, t_r = 2.5, 1.0 / 1600.0, 5e-3
-    dt, dtau, tol, tol_switch = 1e-2, 1e-3, args.dual_tol, 5e-6
-    refine = args.dual_tol < tol_switch
+    dt, dtau, tol, tol_switch = 1e-2, args.dual_dtau, args.dual_tol, 5e-6
+    prec = abi.FR_F64 if args.dual_precision == 64 else abi.FR_F32
+    refine = prec == abi.FR_F32 and args.dual_tol < tol_switch
     n_warm, n_collect, n_held = 3, args.dual_collect_steps, args.dual_held_steps
     per_step = max(1, args.dual_samples // n_collect)
-    U0 = W.taylor_green(n, lo, hi, order, dtype=np.float32)
+    U0 = W.taylor_green(n, lo, hi, order, dtype=np.float32 if prec == abi.FR_F32 else np.float64)
     solvers = []
     for _ in range(2):
-        c32 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, abi.FR_F32)
-        c64 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, abi.FR_F64)
-        solvers.append([c32, c64, abi.pack_state(c32, U0, abi.FR_F32), abi.new_state(c64, abi.FR_F64)])
+        c32 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, prec)
+        c64 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, abi.FR_F64) if refine else None
+        solvers.append([c32, c64, abi.pack_state(c32, U0, prec),
+                        abi.new_state(c64, abi.FR_F64) if refine else None])
     abi.fr_dual_init(solvers[0][0], solvers[0][2])
-    net = abi.fr_mlp_create(solvers[0][0], 256, per_step * n_collect, seed=2021)
+    net = abi.fr_mlp_create(solvers[0][0], args.dual_hidden, per_step * n_collect, seed=2021)
     log = {"A": [], "B": []}
 
     def step(k, which, guess, max_iter):
@@ -452,8 +456,8 @@ def run_dual(args):
             abi.fr_mlp_collect(net, per_step, seed=1000 + k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    loss0 = abi.fr_mlp_train(net, 1, 1e-3)
-    loss = abi.fr_mlp_train(net, args.dual_epochs - 1, 1e-3)
+    loss0 = abi.fr_mlp_train(net, 1, args.dual_lr)
+    loss = abi.fr_mlp_train(net, args.dual_epochs - 1, args.dual_lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     abi.fr_dual_copy(solvers[1][0], solvers[0][0])
@@ -470,14 +474,15 @@ def run_dual(args):
     dv = float((Va - Vb).abs().max().item())
     out = {
         "metric": f"wall-s per physical step at {tol:g} residual", "value": wb, "unit": "s",
-        "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"hex_p4_{args.dual_mesh}cube_dual", "order": order,
+        "higher_is_better": False, "n_gpus": 1,
+        "dtype": "f64" if prec == abi.FR_F64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"hex_p{order}_{args.dual_mesh}cube_dual", "order": order,
                    "mesh": list(n), "dt": dt, "dtau": dtau, "tol": tol,
                    "tol_switch": tol_switch, "bdf": 2, "pseudo": "RK4",
                    "max_iter_train_steps": args.dual_train_iters,
                    "max_iter_held_steps": args.dual_held_iters,
-                   "mlp": {"hidden": 256, "samples": per_step * n_collect,
-                           "epochs": args.dual_epochs, "lr": 1e-3, "train_s": t_train,
+                   "mlp": {"hidden": args.dual_hidden, "samples": per_step * n_collect,
+                           "epochs": args.dual_epochs, "lr": args.dual_lr, "train_s": t_train,
                            "loss_first": loss0, "loss_last": loss}},
         "plain_wall_s": wa, "learned_wall_s": wb, "speedup": wa / wb,
         "held_out_steps": n_held, "max_velocity_difference": dv,
@@ -486,7 +491,8 @@ def run_dual(args):
     print(json.dumps(out))
     for c32, c64, _, _ in solvers:
         abi.fr_destroy(c32)
-        abi.fr_destroy(c64)
+        if c64 is not None:
+            abi.fr_destroy(c64)
     abi.fr_mlp_destroy(net)
 
 
@@ -628,6 +634,11 @@ def main():
     ap.add_argument("--rk-mesh", type=int, default=None,
                     help="elements per direction (default: the order sweep's mesh)")
     ap.add_argument("--dual-mesh", type=int, default=48)
+    ap.add_argument("--dual-order", type=int, default=4)
+    ap.add_argument("--dual-dtau", type=float, default=1e-3)
+    ap.add_argument("--dual-precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--dual-hidden", type=int, default=256)
+    ap.add_argument("--dual-lr", type=float, default=1e-3)
     ap.add_argument("--dual-collect-steps", type=int, default=8)
     ap.add_argument("--dual-held-steps", type=int, default=5)
     ap.add_argument("--dual-samples", type=int, default=5000)

@@ -267,7 +267,9 @@ typedef struct fr_dual_opts {
     fr_ctx* refine;       /* NULL, or the FP64 refinement context */
     void* U_refine;       /* refine's work state */
     double tol_switch;    /* residual at which ctx hands over to refine */
-    fr_mlp* mlp;          /* trained network for FR_GUESS_MLP */
+    fr_mlp* mlp;          /* trained network for FR_GUESS_MLP (created on this
+                             context or one of the same discretization; the
+                             guess comes from this context's history) */
 } fr_dual_opts;
 
 typedef struct fr_dual_stats {
@@ -310,6 +312,11 @@ int fr_dual_copy(fr_ctx* dst, const fr_ctx* src, void* stream);
  *                   1e-8, step lr); *loss is the loss before the last step.
  *   fr_mlp_predict  guess of the next level from ctx's three newest levels:
  *                   U (context precision) and V (FP64 velocity rows).
+ *   fr_mlp_predict_for  the same from the history of another context `ctx`
+ *                   of the same discretization (dimension, order, elements,
+ *                   precision; FR_EINVAL otherwise), e.g. a second solver
+ *                   that shares the trained network.  fr_dual_step with
+ *                   FR_GUESS_MLP uses its own context's history this way.
  *   fr_mlp_params   copy to (set = 0) or from (set != 0) host memory:
  *                   which 0 = parameters, 1 = gradients (count = the total
  *                   from fr_mlp_info, order W1 b1 W2 b2 W3 b3, W row-major
@@ -327,6 +334,7 @@ int fr_mlp_collect(fr_mlp* mlp, int count, unsigned long long seed, int* elems, 
 int fr_mlp_loss_grad(fr_mlp* mlp, double* loss, void* stream);
 int fr_mlp_train(fr_mlp* mlp, int epochs, double lr, double* loss, void* stream);
 int fr_mlp_predict(fr_mlp* mlp, void* U, double* V, void* stream);
+int fr_mlp_predict_for(fr_mlp* mlp, fr_ctx* ctx, void* U, double* V, void* stream);
 int fr_mlp_params(fr_mlp* mlp, int which, float* host, size_t count, int set);
 
 /* The tensor-core GEMM of the MLP as a utility: C[N x M] = A . B in FP32

@@ -26,7 +26,7 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", 
            "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error", "fr_rhs_static",
            "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity", "fr_dual_copy",
            "fr_mlp_create", "fr_mlp_destroy", "fr_mlp_info", "fr_mlp_collect", "fr_mlp_loss_grad",
-           "fr_mlp_train", "fr_mlp_predict", "fr_mlp_params", "fr_gemm_bf16"]
+           "fr_mlp_train", "fr_mlp_predict", "fr_mlp_predict_for", "fr_mlp_params", "fr_gemm_bf16"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -95,6 +95,7 @@ def _lib():
         lib.fr_mlp_loss_grad.argtypes = [vp, dp, vp]
         lib.fr_mlp_train.argtypes = [vp, i32, dbl, dp, vp]
         lib.fr_mlp_predict.argtypes = [vp, vp, vp, vp]
+        lib.fr_mlp_predict_for.argtypes = [vp, vp, vp, vp, vp]
         lib.fr_mlp_params.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float), sz, i32]
         lib.fr_gemm_bf16.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.c_longlong, vp,
                                      ctypes.c_longlong, vp, ctypes.c_longlong, vp]
@@ -322,6 +323,11 @@ def fr_mlp_train(mlp, epochs, lr, stream=None):
 def fr_mlp_predict(mlp, U, V, stream=None):
     _check(_lib().fr_mlp_predict(ctypes.c_void_p(mlp), _ptr(U), _ptr(V), _stream(stream)),
            "fr_mlp_predict")
+
+
+def fr_mlp_predict_for(mlp, ctx, U, V, stream=None):
+    _check(_lib().fr_mlp_predict_for(ctypes.c_void_p(mlp), ctypes.c_void_p(ctx), _ptr(U), _ptr(V),
+                                     _stream(stream)), "fr_mlp_predict_for")
 
 
 def fr_mlp_params(mlp, which, values=None, count=None):

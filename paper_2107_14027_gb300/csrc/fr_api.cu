@@ -591,7 +591,8 @@ int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, 
     // the network's guess competes with the extrapolation on the residual
     if ((st = alloc_zeroed(&c->guess_u, c->bytes_state, "guess")) != FR_OK) return st;
     if ((st = alloc_zeroed((void**)&c->guess_v, nv * sizeof(double), "guess")) != FR_OK) return st;
-    if ((st = fr_mlp_predict(o->mlp, c->guess_u, c->guess_v, stream)) != FR_OK) return st;
+    // the guess of this context's next level, from this context's history
+    if ((st = fr_mlp_predict_for(o->mlp, c, c->guess_u, c->guess_v, stream)) != FR_OK) return st;
     st = guess_residual(c, U, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
                         &stats.res_guess[0], s);
     if (st == FR_OK)

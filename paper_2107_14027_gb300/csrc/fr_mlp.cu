@@ -462,8 +462,17 @@ int fr_mlp_train(fr_mlp* q, int epochs, double lr, double* loss, void* stream) {
 }
 
 int fr_mlp_predict(fr_mlp* q, void* U, double* V, void* stream) {
-  if (!q || !ptr16(U) || !ptr16(V)) return FR_EINVAL;
-  fr_ctx* c = q->ctx;
+  if (!q) return FR_EINVAL;
+  return fr_mlp_predict_for(q, q->ctx, U, V, stream);
+}
+
+int fr_mlp_predict_for(fr_mlp* q, fr_ctx* c, void* U, double* V, void* stream) {
+  if (!q || !c || !ptr16(U) || !ptr16(V)) return FR_EINVAL;
+  // any context of the network's discretization (its history is read)
+  const fr_ctx* o = q->ctx;
+  if (c->dim != o->dim || c->order != o->order || c->nv != o->nv || c->ne != o->ne ||
+      c->stride != o->stride || c->precision != o->precision)
+    return FR_EINVAL;
   if (c->hist_levels < 3 || !q->scales_set || q->adam_t == 0) return FR_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long ld = (long long)c->stride;

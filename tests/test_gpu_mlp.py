@@ -233,3 +233,47 @@ def test_learned_guess_gain_over_extrapolation(abi):
     # the learned run needs fewer pseudo iterations in total
     assert chosen >= 1
     assert sum(r[0] for r in runs["mlp"][10:]) < sum(r[0] for r in runs["plain"][10:])
+
+
+def test_learned_guess_reads_the_stepping_context_history(abi):
+    """A network trained on context A and used by forks B and C of A (same
+    history): each fork's guess comes from its own history, so B and C get
+    the same guess even after A has moved on, and a context of another
+    discretization is refused."""
+    n, order, nv = (4, 3, 3), 2, 13
+    U0, mesh, prm, lo, hi = parity.make_case(n, order)
+    dt, dtau, tol = 1e-2, 1e-2, 1e-8
+    ctxs = [abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, 64) for _ in range(3)]
+    other = abi.fr_create(n, lo, hi, order + 1, nv, prm.zeta, prm.nu, prm.T, 64)
+    A, B, C = ctxs
+    net = abi.fr_mlp_create(A, 32, 256, seed=7)
+    try:
+        Ua = abi.pack_state(A, U0, 64)
+        abi.fr_dual_init(A, Ua)
+        for k in range(5):
+            abi.fr_dual_step(A, Ua, dt, dtau, tol, 40, check_every=10, allow_noconv=True)
+            if k >= 2:
+                abi.fr_mlp_collect(net, 24, seed=k)
+        abi.fr_mlp_train(net, 20, 1e-3)
+        abi.fr_dual_copy(B, A)
+        abi.fr_dual_copy(C, A)
+        Ub, Uc = Ua.clone(), Ua.clone()
+        # C steps with the learned guess before A moves on; B after
+        _, sc = abi.fr_dual_step(C, Uc, dt, dtau, tol, 3, check_every=3, guess=abi.FR_GUESS_MLP,
+                                 mlp=net, allow_noconv=True)
+        abi.fr_dual_step(A, Ua, dt, dtau, tol, 40, check_every=10, allow_noconv=True)
+        _, sb = abi.fr_dual_step(B, Ub, dt, dtau, tol, 3, check_every=3, guess=abi.FR_GUESS_MLP,
+                                 mlp=net, allow_noconv=True)
+        torch.cuda.synchronize()
+        assert np.isfinite(sb.res_guess[1])
+        assert sb.res_guess[1] == sc.res_guess[1] and sb.res_guess[0] == sc.res_guess[0]
+        assert torch.equal(Ub, Uc)
+        Uo = abi.new_state(other, 64)
+        Vo = abi.new_velocity(other, 3, order + 1)
+        with pytest.raises(abi.FrError) as ei:
+            abi.fr_mlp_predict_for(net, other, Uo, Vo)
+        assert ei.value.status == abi.FR_EINVAL
+    finally:
+        abi.fr_mlp_destroy(net)
+        for c in ctxs + [other]:
+            abi.fr_destroy(c)
