@@ -277,3 +277,47 @@ def test_learned_guess_reads_the_stepping_context_history(abi):
         abi.fr_mlp_destroy(net)
         for c in ctxs + [other]:
             abi.fr_destroy(c)
+
+
+def test_learned_guess_gain_in_3d_through_a_fork(abi):
+    """3-D p = 2, 8^3 Taylor-Green (zeta 2.5, nu 1/1600, T_r 5e-3), BDF2
+    dt = 1e-2, RK4 dtau = 1e-2 to 1e-6, FP64.  Solver A takes 3 steps, then 7
+    more while element samples are collected, trains the network, and a fork
+    B of A (same history) takes the held-out steps with the learned guess
+    while A takes them with the extrapolation."""
+    from paper_2107_14027_gb300 import workloads as W
+    n, order, nv = (8, 8, 8), 2, 13
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    U0 = W.taylor_green(n, lo, hi, order)
+    A = abi.fr_create(n, lo, hi, order, nv, 2.5, 1 / 1600, 5e-3, 64)
+    B = abi.fr_create(n, lo, hi, order, nv, 2.5, 1 / 1600, 5e-3, 64)
+    net = abi.fr_mlp_create(A, 256, 4096, seed=2021)
+    dt, dtau, tol = 1e-2, 1e-2, 1e-6
+    try:
+        Ua = abi.pack_state(A, U0, 64)
+        Ub = Ua.clone()
+        abi.fr_dual_init(A, Ua)
+        for k in range(1, 11):
+            st, _ = abi.fr_dual_step(A, Ua, dt, dtau, tol, 6000, check_every=5)
+            if k > 3:
+                abi.fr_mlp_collect(net, 4096 // 7, seed=1000 + k)
+        abi.fr_mlp_train(net, 300, 2e-3)
+        abi.fr_dual_copy(B, A)
+        plain, learned, chosen = [], [], 0
+        for k in range(4):
+            _, sa = abi.fr_dual_step(A, Ua, dt, dtau, tol, 6000, check_every=5)
+            _, sb = abi.fr_dual_step(B, Ub, dt, dtau, tol, 6000, check_every=5,
+                                     guess=abi.FR_GUESS_MLP, mlp=net)
+            assert sa.res < tol and sb.res < tol
+            assert min(sb.res_guess) == (sb.res_guess[1] if sb.guess_used == abi.FR_GUESS_MLP
+                                         else sb.res_guess[0])
+            chosen += sb.guess_used == abi.FR_GUESS_MLP
+            plain.append(sa.iters)
+            learned.append(sb.iters)
+        print("plain", plain, "learned", learned)
+        assert chosen >= 1
+        assert sum(learned) < 0.8 * sum(plain)
+    finally:
+        abi.fr_mlp_destroy(net)
+        abi.fr_destroy(A)
+        abi.fr_destroy(B)
