@@ -170,7 +170,14 @@ int fr_rhs_unfused(fr_ctx* ctx, const void* U, void* R, void* stream);
 /* fr_rhs on HOST buffers: copies U (bytes_per_state bytes, host memory,
  * preferably pinned) to context-owned device staging, evaluates the fused
  * RHS and copies R back to host memory.  Synchronises `stream` before
- * returning.  Allocates the staging on first use. */
+ * returning.  Allocates the staging on first use.  Meshes of at least two
+ * slabs (element ranges of whole 32-element tiles, each one element layer
+ * plus a tile; up to 4) are pipelined: each slab is copied in, traced,
+ * computed and copied out as soon as its data and its neighbours' traces
+ * are there, on three internal streams ordered after `stream`, so copies in
+ * both directions overlap each other and the kernels.  Only the real
+ * elements' columns of R_host are written (the padding to elem_stride is
+ * left as it was). */
 int fr_rhs_host(fr_ctx* ctx, const void* U_host, void* R_host, void* stream);
 
 /* One classical RK4 step in pseudo time of dU/dtau = R(U) (Sec. 5, read as

@@ -105,6 +105,89 @@ int fused_stage(fr_ctx* c, int stage, void* U, acmhd::StageArgs a, cudaStream_t 
                      "fused stage");
 }
 
+// Host-buffer RHS pipeline.  The elements are cut into S slabs of whole
+// 32-element tiles, each at least one element layer (z-plane in 3-D, x-row
+// in 2-D) plus a tile, so the face neighbours of a slab lie in the two
+// adjacent slabs (periodically).  Each slab is copied in, its traces are
+// computed as soon as it has arrived, its volume work runs once its
+// neighbours' traces exist (slabs 1 .. S-1, then 0, which needs the last
+// slab's traces), and its R is copied out while later slabs are still
+// arriving or being computed: copies in both directions and the kernels
+// overlap on three streams.
+using acmhd::kHostSlabsMax;
+
+int host_slabs(const fr_ctx* c, int* bounds) {
+  const long long layer = c->dim == 3 ? (long long)c->mesh.n[0] * c->mesh.n[1] : c->mesh.n[0];
+  const long long ntile = (c->ne + 31) / 32;
+  const long long min_tiles = (layer + 31) / 32 + 1;
+  int S = kHostSlabsMax;
+  while (S > 1 && ntile / S < min_tiles) --S;
+  for (int i = 0; i <= S; ++i) {
+    const long long b = ntile * i / S * 32;
+    bounds[i] = (int)(b < c->ne ? b : c->ne);
+  }
+  return S;
+}
+
+int ensure_host_pipeline(fr_ctx* c) {
+  if (c->hs_ready) return FR_OK;
+  for (int i = 0; i < 3; ++i) {
+    int st = cuda_status(cudaStreamCreateWithFlags(&c->hs[i], cudaStreamNonBlocking),
+                         "pipeline streams");
+    if (st != FR_OK) return st;
+  }
+  for (int i = 0; i < 2 * kHostSlabsMax + 2; ++i) {
+    int st = cuda_status(cudaEventCreateWithFlags(&c->hev[i], cudaEventDisableTiming),
+                         "pipeline events");
+    if (st != FR_OK) return st;
+  }
+  c->hs_ready = 1;
+  return FR_OK;
+}
+
+// One slab's rows between the padded host and device layouts: nv m^d rows of
+// (e_end - e_begin) values at pitch elem_stride.
+cudaError_t copy_slab(const fr_ctx* c, void* dst, const void* src, int e_begin, int e_end,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+  const size_t pitch = c->stride * c->elem_bytes, off = (size_t)e_begin * c->elem_bytes;
+  return cudaMemcpy2DAsync(static_cast<char*>(dst) + off, pitch,
+                           static_cast<const char*>(src) + off, pitch,
+                           (size_t)(e_end - e_begin) * c->elem_bytes, (size_t)c->nv * c->npts,
+                           kind, s);
+}
+
+int rhs_host_pipelined(fr_ctx* c, const void* U_host, void* R_host, const int* b, int S,
+                       cudaStream_t s) {
+  cudaStream_t in = c->hs[0], k = c->hs[1], out = c->hs[2];
+  cudaEvent_t* ev_in = c->hev;
+  cudaEvent_t* ev_done = c->hev + kHostSlabsMax;
+  cudaEvent_t ev_start = c->hev[2 * kHostSlabsMax], ev_end = c->hev[2 * kHostSlabsMax + 1];
+  cudaError_t e = cudaEventRecord(ev_start, s);  // after the caller's earlier work
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->hs[i], ev_start, 0);
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    e = copy_slab(c, c->host_u, U_host, b[i], b[i + 1], cudaMemcpyHostToDevice, in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[i], in);
+  }
+  auto volume = [&](int i) {
+    cudaError_t r = acmhd::launch_fused_range(c, c->host_u, c->trace, c->host_r, b[i], b[i + 1], k);
+    if (r == cudaSuccess) r = cudaEventRecord(ev_done[i], k);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(out, ev_done[i], 0);
+    if (r == cudaSuccess) r = copy_slab(c, R_host, c->host_r, b[i], b[i + 1],
+                                        cudaMemcpyDeviceToHost, out);
+    return r;
+  };
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    e = cudaStreamWaitEvent(k, ev_in[i], 0);
+    if (e == cudaSuccess) e = acmhd::launch_trace_range(c, c->host_u, c->trace, b[i], b[i + 1], k);
+    if (e == cudaSuccess && i >= 2) e = volume(i - 1);  // traces i-2 .. i exist
+  }
+  if (e == cudaSuccess && S >= 2) e = volume(S - 1);    // needs traces S-2, S-1, 0
+  if (e == cudaSuccess) e = volume(0);                    // needs traces S-1, 0, 1
+  if (e == cudaSuccess) e = cudaEventRecord(ev_end, out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_end, 0);
+  return cuda_status(e, "host-buffer pipeline");
+}
+
 // Pseudo steps with the update fused into the volume kernel: on request, and
 // by default at p <= 3.  Measured on GB300 (FP32 RK4 steps on the 3-D order
 // sweep meshes of about 38M points per variable, fused / separate):
@@ -301,6 +384,10 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
 void fr_destroy(fr_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  if (c->hs_ready) {
+    for (int i = 0; i < 3; ++i) cudaStreamDestroy(c->hs[i]);
+    for (int i = 0; i < 2 * kHostSlabsMax + 2; ++i) cudaEventDestroy(c->hev[i]);
+  }
   void* bufs[] = {c->trace, c->rk_stage, c->rk_acc, c->rk_k, c->rk_stage2, c->trace2,
                   c->stage_partial, c->unf_uf, c->unf_f,
                   c->unf_div, c->unf_fi, c->host_u, c->host_r, c->err,
@@ -373,6 +460,14 @@ int fr_rhs_host(fr_ctx* c, const void* U_host, void* R_host, void* stream) {
   if ((st = alloc_zeroed(&c->host_u, c->bytes_state, "host staging")) != FR_OK) return st;
   if ((st = alloc_zeroed(&c->host_r, c->bytes_state, "host staging")) != FR_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int bounds[kHostSlabsMax + 1];
+  const int S = host_slabs(c, bounds);
+  if (S > 1 && c->schedule != FR_SCHEDULE_SWEEP) {
+    if ((st = ensure_host_pipeline(c)) != FR_OK) return st;
+    st = rhs_host_pipelined(c, U_host, R_host, bounds, S, s);
+    if (st == FR_OK) st = cuda_status(cudaStreamSynchronize(s), "stream synchronize");
+    return st;
+  }
   st = cuda_status(cudaMemcpyAsync(c->host_u, U_host, c->bytes_state, cudaMemcpyHostToDevice, s),
                    "copy to device");
   if (st == FR_OK) st = fr_rhs(c, c->host_u, c->host_r, stream);

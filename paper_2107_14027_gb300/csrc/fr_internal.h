@@ -49,6 +49,13 @@ struct FrConst {
   int stride;      // elem_stride
 };
 
+// most slabs of the host-buffer RHS pipeline (fr_rhs_host).  Measured on
+// GB300 (64^3 p=3 FP32, 872 MB each way): 1 slab 9.43 ms per call, 2 9.07,
+// 3 8.99, 4 8.61, 8 9.71.  A slab's copy is one 2-D copy of nv m^d row
+// segments; narrower segments copy more slowly (8 slabs: 6.9 ms in, 6.0 ms
+// out, against 4.1 ms for one contiguous copy), which cancels the overlap.
+constexpr int kHostSlabsMax = 4;
+
 // ring slot of the level `back` steps before the newest one
 inline int hist_slot(int head, int back) { return (head + 4 - back) % 4; }
 
@@ -112,6 +119,9 @@ struct fr_ctx {
   void* unf_fi;        // unfused: common flux [2d][nv][m^(d-1)][stride]
   void* host_u;        // fr_rhs_host device staging
   void* host_r;
+  cudaStream_t hs[3];  // fr_rhs_host pipeline: copies in, kernels, copies out
+  cudaEvent_t hev[2 * acmhd::kHostSlabsMax + 2];  // per slab: in, computed; start; done
+  int hs_ready;
   int* err;            // device error word (bounded waits)
   // dual time stepping (FP64 velocity rows: dim * npts * stride doubles)
   double* dual_vs;     // RK4 stage velocity
@@ -138,6 +148,11 @@ namespace acmhd {
 cudaError_t launch_trace(const fr_ctx* c, const void* U, void* trace, cudaStream_t s);
 cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* trace, void* R,
                          cudaStream_t s);
+// The same on the elements [e_begin, e_end) only (e_begin a multiple of 32).
+cudaError_t launch_trace_range(const fr_ctx* c, const void* U, void* trace, int e_begin,
+                               int e_end, cudaStream_t s);
+cudaError_t launch_fused_range(const fr_ctx* c, const void* U, const void* trace, void* R,
+                               int e_begin, int e_end, cudaStream_t s);
 cudaError_t launch_unfused(const fr_ctx* c, const void* U, void* R, cudaStream_t s);
 cudaError_t launch_sweep(const fr_ctx* c, const void* U, void* Tr, void* R, const SweepPlan& p,
                          unsigned epoch, cudaStream_t s);

@@ -24,19 +24,20 @@ constexpr bool trace_stages_pv() {
 
 template <int D, int M, typename T, int E, int EF>
 __global__ void __launch_bounds__(256)
-trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c) {
+trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c, int tile0) {
   constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
   constexpr bool PV = trace_stages_pv<D, M, T>();
   __shared__ T sPV[PV ? (1 + D) * NP * E : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int el = lane % E;
-  const int e = blockIdx.x * E + el;
+  const int tile = tile0 + blockIdx.x;
+  const int e = tile * E + el;
   const int sub = lane / E;
   if constexpr (PV) {
     // rows of E contiguous elements; the tile lies inside the padded stride
     for (int idx = threadIdx.x; idx < (1 + D) * NP * E; idx += blockDim.x) {
       const int row = idx / E, x = idx - row * E;
-      sPV[idx] = __ldg(U + (size_t)row * c.stride + blockIdx.x * E + x);
+      sPV[idx] = __ldg(U + (size_t)row * c.stride + tile * E + x);
     }
     __syncthreads();
   }
@@ -76,23 +77,33 @@ trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c) {
   }
 }
 
+// elements [e_begin, e_end); e_begin a multiple of 32
 template <int D, int M, typename T>
-cudaError_t trace_launch(const fr_ctx* ctx, const FrConst<T>& c, const void* U, void* Tr,
+cudaError_t trace_launch(const FrConst<T>& c, const void* U, void* Tr, int e_begin, int e_end,
                          cudaStream_t s) {
   constexpr int E = 32;
-  const int nblk = (ctx->ne + E - 1) / E;
+  const int nblk = (e_end - e_begin + E - 1) / E;
+  if (nblk <= 0) return cudaSuccess;
   trace_kernel<D, M, T, E, FusedCfg<D, M, T>::E>
-      <<<nblk, 256, 0, s>>>(static_cast<const T*>(U), static_cast<T*>(Tr), c);
+      <<<nblk, 256, 0, s>>>(static_cast<const T*>(U), static_cast<T*>(Tr), c, e_begin / E);
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace(const fr_ctx* c, const void* U, void* Tr, cudaStream_t s) {
+cudaError_t launch_trace_range(const fr_ctx* c, const void* U, void* Tr, int e_begin, int e_end,
+                               cudaStream_t s) {
+  if (e_begin % 32 != 0) return cudaErrorInvalidValue;
   if (c->precision == FR_F32) {
-    ACMHD_DISPATCH_DM(c->dim, c->m, return (trace_launch<D_, M_, float>(c, c->cf, U, Tr, s)));
+    ACMHD_DISPATCH_DM(c->dim, c->m,
+                      return (trace_launch<D_, M_, float>(c->cf, U, Tr, e_begin, e_end, s)));
   } else {
-    ACMHD_DISPATCH_DM(c->dim, c->m, return (trace_launch<D_, M_, double>(c, c->cd, U, Tr, s)));
+    ACMHD_DISPATCH_DM(c->dim, c->m,
+                      return (trace_launch<D_, M_, double>(c->cd, U, Tr, e_begin, e_end, s)));
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_trace(const fr_ctx* c, const void* U, void* Tr, cudaStream_t s) {
+  return launch_trace_range(c, U, Tr, 0, c->ne, s);
 }
 
 }  // namespace acmhd
