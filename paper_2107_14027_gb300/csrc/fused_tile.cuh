@@ -324,4 +324,42 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
   }
 }
 
+// The fused RHS kernel: one tile of E elements per CTA.  RANGED kernels
+// start at tile tile0 (the host-buffer pipeline runs the mesh in slabs);
+// the whole-mesh kernel keeps the tile index free of the offset (measured:
+// the offset alone cost 2 % of the 64^3 p=3 volume kernel's time).
+template <int D, int M, typename T, int E, int NW, int MINB, bool RANGED>
+__global__ void __launch_bounds__(NW * 32, MINB)
+fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ R,
+             const FrConst<T> c, int tile0) {
+  constexpr int NP = ipow<M>(D);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);  // [1+D][NP][E]
+  T* sA = sU + (1 + D) * NP * E;           // [1+D][NP][E]
+  RhsOut<T> out{R};
+  const int tile = RANGED ? tile0 + (int)blockIdx.x : (int)blockIdx.x;
+  fused_tile<D, M, T, E, NW, false>(U, Tr, out, c, tile * E, sU, sA);
+}
+
+// elements [e_begin, e_end); e_begin a multiple of 32 (and so of E), and 0
+// unless RANGED
+template <int D, int M, typename T, bool RANGED>
+cudaError_t fused_launch(const FrConst<T>& c, const void* U, const void* Tr, void* R, int e_begin,
+                         int e_end, cudaStream_t s) {
+  using C = FusedCfg<D, M, T>;
+  auto kern = fused_kernel<D, M, T, C::E, C::NW, C::MINB, RANGED>;
+  static bool attr_done = false;  // per template instance
+  if (!attr_done) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)C::SMEM);
+    if (err != cudaSuccess) return err;
+    attr_done = true;
+  }
+  const int nblk = (e_end - e_begin + C::E - 1) / C::E;
+  if (nblk <= 0) return cudaSuccess;
+  kern<<<nblk, C::NW * 32, C::SMEM, s>>>(static_cast<const T*>(U), static_cast<const T*>(Tr),
+                                          static_cast<T*>(R), c, e_begin / C::E);
+  return cudaGetLastError();
+}
+
 }  // namespace acmhd

@@ -98,18 +98,6 @@ __device__ __forceinline__ void trace_tile(const T* __restrict__ U, T* __restric
 
 template <int D, int M, typename T, int E, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB)
-fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ R,
-             const FrConst<T> c, int tile0) {
-  constexpr int NP = ipow<M>(D);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sU = reinterpret_cast<T*>(smem_raw);  // [1+D][NP][E]
-  T* sA = sU + (1 + D) * NP * E;           // [1+D][NP][E]
-  RhsOut<T> out{R};
-  fused_tile<D, M, T, E, NW, false>(U, Tr, out, c, (tile0 + blockIdx.x) * E, sU, sA);
-}
-
-template <int D, int M, typename T, int E, int NW, int MINB>
-__global__ void __launch_bounds__(NW * 32, MINB)
 sweep_kernel(const T* __restrict__ U, T* __restrict__ Tr, T* __restrict__ R, const FrConst<T> c,
              const int* __restrict__ units, int nunits, unsigned* __restrict__ flags,
              unsigned epoch, int ntiles, int K, unsigned* __restrict__ queue, int* __restrict__ err) {
@@ -156,26 +144,6 @@ sweep_kernel(const T* __restrict__ U, T* __restrict__ Tr, T* __restrict__ R, con
   }
 }
 
-// elements [e_begin, e_end); e_begin a multiple of 32 (and so of E)
-template <int D, int M, typename T>
-cudaError_t fused_launch(const FrConst<T>& c, const void* U, const void* Tr, void* R, int e_begin,
-                         int e_end, cudaStream_t s) {
-  using C = FusedCfg<D, M, T>;
-  auto kern = fused_kernel<D, M, T, C::E, C::NW, C::MINB>;
-  static bool attr_done = false;  // per template instance
-  if (!attr_done) {
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::SMEM);
-    if (err != cudaSuccess) return err;
-    attr_done = true;
-  }
-  const int nblk = (e_end - e_begin + C::E - 1) / C::E;
-  if (nblk <= 0) return cudaSuccess;
-  kern<<<nblk, C::NW * 32, C::SMEM, s>>>(static_cast<const T*>(U), static_cast<const T*>(Tr),
-                                          static_cast<T*>(R), c, e_begin / C::E);
-  return cudaGetLastError();
-}
-
 template <int D, int M, typename T>
 cudaError_t sweep_launch(const fr_ctx* ctx, const FrConst<T>& c, const void* U, void* Tr,
                          void* R, const SweepPlan& p, unsigned epoch, cudaStream_t s) {
@@ -201,21 +169,15 @@ cudaError_t sweep_launch(const fr_ctx* ctx, const FrConst<T>& c, const void* U, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_fused_range(const fr_ctx* c, const void* U, const void* Tr, void* R,
-                               int e_begin, int e_end, cudaStream_t s) {
-  if (e_begin % 32 != 0) return cudaErrorInvalidValue;
+cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* Tr, void* R, cudaStream_t s) {
   if (c->precision == FR_F32) {
     ACMHD_DISPATCH_DM(c->dim, c->m,
-                      return (fused_launch<D_, M_, float>(c->cf, U, Tr, R, e_begin, e_end, s)));
+                      return (fused_launch<D_, M_, float, false>(c->cf, U, Tr, R, 0, c->ne, s)));
   } else {
     ACMHD_DISPATCH_DM(c->dim, c->m,
-                      return (fused_launch<D_, M_, double>(c->cd, U, Tr, R, e_begin, e_end, s)));
+                      return (fused_launch<D_, M_, double, false>(c->cd, U, Tr, R, 0, c->ne, s)));
   }
   return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* Tr, void* R, cudaStream_t s) {
-  return launch_fused_range(c, U, Tr, R, 0, c->ne, s);
 }
 
 cudaError_t launch_sweep(const fr_ctx* c, const void* U, void* Tr, void* R, const SweepPlan& p,
