@@ -200,6 +200,7 @@ print(json.dumps({{"t": dt, "reps": k, "dof": U.size}}))
 def run_reference(args):
     if not _reference_runs_here():
         return
+    _, _, world = _rank_env()
     # one oracle RHS on a 12^3-element p = 3 sample of the 64^3 workload per step
     n_side = 12
     code_steps = args.warmup + args.steps

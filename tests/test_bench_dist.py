@@ -69,3 +69,23 @@ def test_single_process_needs_no_process_group(monkeypatch):
     assert bench._max_over_ranks(None, 2.5, "cpu") == 2.5
     assert bench._job_rate(10.0, 1, 2.0) == 5.0
     assert bench._reference_runs_here()
+
+
+def test_reference_arm_prints_one_json_line():
+    """bench.py --impl reference (the FP64 oracle on host cores) at N = 1."""
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    for v in ("RANK", "LOCAL_RANK", "WORLD_SIZE"):
+        env.pop(v, None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
+                       env=env, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference" and out["n_gpus"] == 1 and out["value"] > 0
+    assert out["cpu_baseline"]["kind"] == "oracle"
+    assert out["e2e"]["h2d_bytes_per_step"] == 0
