@@ -134,6 +134,50 @@ def test_full_size_hex_p3_64cube_sampled(abi, precision):
     parity.assert_parity(R[:, :, elems], R_ref, scale, precision, plain=False, label="64^3")
 
 
+FULL_SIZE = [(1, 168, 32), (2, 112, 32), (3, 84, 32), (4, 67, 32), (5, 56, 32), (6, 48, 32),
+             (4, 48, 32), (4, 48, 64)]
+
+
+@pytest.mark.parametrize("order,nside,precision", FULL_SIZE)
+def test_full_size_order_sweep_and_dual_mesh_sampled(abi, order, nside, precision):
+    """The order-sweep meshes (about 38M points per variable, p = 1..6) and
+    the dual-time workload's p = 4, 48^3 mesh at full size, in the launch
+    configuration of their benchmarks (fr_rhs, two kernels); 256 sampled
+    elements, including the mesh corners and the last CTA, against the
+    oracle's per-element path."""
+    from paper_2107_14027_gb300 import workloads as W
+    n = (nside,) * 3
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    m = order + 1
+    U = W.taylor_green(n, lo, hi, order, dtype=np.float32 if precision == 32 else np.float64)
+    prm = fr.Params(2.5, 1.0 / 1600.0, 5e-3)
+    mesh = fr.Mesh(n, lo, hi)
+    ctx = abi.fr_create(n, lo, hi, order, 13, prm.zeta, prm.nu, prm.T, precision, 0)
+    try:
+        Ud = abi.pack_state(ctx, U, precision)
+        Rd = abi.new_state(ctx, precision, fill=float("nan"))
+        abi.fr_rhs(ctx, Ud, Rd)
+        torch.cuda.synchronize()
+        stride, ne, _ = abi.fr_layout(ctx)
+        rng = np.random.default_rng(order)
+        elems = np.unique(np.concatenate([[0, nside - 1, nside * (nside - 1), ne - nside, ne - 1,
+                                           (ne - 1) // 32 * 32],
+                                          rng.choice(ne, 250, replace=False)]))
+        idx = torch.as_tensor(elems, device="cuda")
+        R = Rd[:, :ne].index_select(1, idx).cpu().numpy().astype(np.float64)
+        R = R.reshape(13, m ** 3, len(elems))
+        del Ud, Rd
+    finally:
+        abi.fr_destroy(ctx)
+    assert np.all(np.isfinite(R))
+    U64 = U.astype(np.float64)
+    del U
+    R_ref = fr.rhs_dense(U64, mesh, order, prm, elems=elems)
+    scale = _sampled_term_scale(U64, mesh, order, prm, elems)
+    parity.assert_parity(R, R_ref, scale, precision, plain=False,
+                         label=f"{nside}^3 p={order} f{precision}")
+
+
 def _sampled_term_scale(U, mesh, order, prm, elems):
     from oracle import acmhd
     from oracle.ops1d import Ops1D
