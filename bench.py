@@ -568,6 +568,41 @@ def run_sweep(args):
                       "peak_source": peak_src, "orders": rows}))
 
 
+def run_mlp(args):
+    """The network's GEMMs at the inference shapes of the dual-time workload
+    (p = 4, 48^3: 110,592 elements, 4875 -> 256 -> 256 -> 1625 features):
+    C[N x M] = W[N x K] . X[K x M] in BF16 with FP32 accumulation through
+    fr_gemm_bf16 (the library's tensor-core kernel), against the measured
+    cuBLAS BF16 peak."""
+    import torch
+    from paper_2107_14027_gb300 import abi
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        pk = json.load(f)
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    stream = torch.cuda.current_stream()
+    M = 110592
+    rows, tot_flop, tot_s = [], 0.0, 0.0
+    for N, K in ((256, 4880), (256, 256), (1625, 256)):
+        W = (torch.randn(N, K, device="cuda") * 0.05).to(torch.bfloat16)
+        X = torch.randn(K, M, device="cuda").to(torch.bfloat16)
+        C = torch.empty(N, M, device="cuda", dtype=torch.float32)
+        fn = lambda: abi.fr_gemm_bf16(0, 0, N, M, K, W, K, X, M, C, M, stream)
+        t = _time_loop(fn, stream, args.steps, args.warmup, torch) / args.steps
+        ref = (W.float() @ X.float())
+        err = float((C - ref).abs().max() / ref.abs().max())
+        flop = 2.0 * N * M * K
+        rows.append({"N": N, "M": M, "K": K, "ms": 1e3 * t, "tflops": flop / t / 1e12,
+                     "frac_of_measured_bf16": flop / t / 1e12 / peak, "max_rel_err_vs_fp32": err})
+        tot_flop += flop
+        tot_s += t
+        del W, X, C, ref
+    print(json.dumps({"metric": "BF16 GEMM TFLOP/s, MLP inference shapes", "unit": "TFLOP/s",
+                      "value": tot_flop / tot_s / 1e12, "higher_is_better": True, "n_gpus": 1,
+                      "dtype": "bf16", "data": "synthetic", "steps": args.steps,
+                      "warmup": args.warmup, "peak_tflops": peak, "peak_source": "measured",
+                      "kernel": "mma.sync m16n8k16 BF16, 64x64x32 CTA tiles", "gemms": rows}))
+
+
 def run_rk(args):
     """RK4 pseudo-steps (fr_rk_step) on an N^3 Taylor-Green mesh of order p,
     FP32: the fused-stage schedule (RK4 combination and next-stage traces in
@@ -626,10 +661,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mesh", type=int, default=None,
                     help="profiling only: run fr_rhs on an N^3 mesh and print its timing")
-    ap.add_argument("--workload", default="rhs", choices=["rhs", "dual", "rk", "sweep"],
+    ap.add_argument("--workload", default="rhs", choices=["rhs", "dual", "rk", "sweep", "mlp"],
                     help="rhs: the fused RHS (default); dual: BDF2 dual time stepping, "
                          "plain vs learned initial guess; rk: RK4 pseudo-steps, fused "
-                         "stage vs separate update; sweep: orders 1..6, fused vs unfused")
+                         "stage vs separate update; sweep: orders 1..6, fused vs unfused; "
+                         "mlp: the network's tensor-core GEMMs")
     ap.add_argument("--sweep-orders", default="1,2,3,4,5,6")
     ap.add_argument("--rk-order", type=int, default=3)
     ap.add_argument("--rk-mesh", type=int, default=None,
@@ -663,6 +699,8 @@ def main():
         run_rk(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     else:
         run_gpu(args)
 

@@ -128,6 +128,178 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(const GemmArgs 
       }
 }
 
+// Pipelined kernel for the forward orientation (A[n][k] rows of k, B[k][m]
+// rows of m), used when B's rows start on 16-byte boundaries: 128 x 128
+// output tile per CTA, 8 warps of 64 x 32, K in steps of 32 through two
+// shared-memory stages.  B tiles (the large operand: features or hidden
+// activations of every element) arrive by 16-byte cp.async while the
+// previous stage is multiplied; A tiles (weights, read by every CTA from
+// L2) by cp.async as well when A's rows are 16-byte aligned, else through
+// registers loaded one stage ahead.  Fragments come from ldmatrix (A
+// row-major, B transposed on the fly).  Out-of-range rows and columns are
+// zero-filled (partial copies), so any N, M, K work.
+constexpr int FN = 128, FM = 128, FK = 32, FPAD = 8, FAST_THREADS = 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 16-byte copy global -> shared of which the first `bytes` (0..16) are read
+// and the rest zero-filled
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+
+template <bool A_ALIGNED>
+__global__ void __launch_bounds__(FAST_THREADS) gemm_bf16_fast_kernel(const GemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 sA[2][FN][FK + FPAD];
+  __shared__ __align__(16) __nv_bfloat16 sB[2][FK][FM + FPAD];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wn = warp >> 2, wm = warp & 3;  // warp tile: rows wn*64.., cols wm*32..
+  const int gid = lane >> 2, tig = lane & 3;
+  const int n0 = blockIdx.x * FN, m0 = blockIdx.y * FM;
+  const int nk = (g.K + FK - 1) / FK;
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+
+  // B tile: FK rows of FM values = 512 chunks of 8; thread: 2 chunks
+  auto load_b = [&](int st, int k0) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int q = tid + c * FAST_THREADS;
+      const int k = q / (FM / 8), mc = (q % (FM / 8)) * 8;
+      const long long gk = k0 + k, gm = m0 + mc;
+      int bytes = 0;
+      const __nv_bfloat16* src = g.B;
+      if (gk < g.K && gm < g.M) {
+        const long long left = g.M - gm;
+        bytes = (left >= 8 ? 8 : (int)left) * 2;
+        src = g.B + gk * g.ldb + gm;
+      }
+      cp_async16(&sB[st][k][mc], src, bytes);
+    }
+  };
+  // A tile: FN rows of FK values = 512 chunks of 8; thread: 2 chunks
+  auto load_a_async = [&](int st, int k0) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int q = tid + c * FAST_THREADS;
+      const int n = q / (FK / 8), kc = (q % (FK / 8)) * 8;
+      const long long gn = n0 + n, gk = k0 + kc;
+      int bytes = 0;
+      const __nv_bfloat16* src = g.A;
+      if (gn < g.N && gk < g.K) {
+        const long long left = g.K - gk;
+        bytes = (left >= 8 ? 8 : (int)left) * 2;
+        src = g.A + gn * g.lda + gk;
+      }
+      cp_async16(&sA[st][n][kc], src, bytes);
+    }
+  };
+  __nv_bfloat16 areg[16];  // unaligned A: 16 values per thread and stage
+  auto load_a_regs = [&](int k0) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int q = tid + c * FAST_THREADS;  // 4096 values = FN x FK
+      const int n = q / FK, k = q % FK;
+      const long long gn = n0 + n, gk = k0 + k;
+      areg[c] = (gn < g.N && gk < g.K) ? g.A[gn * g.lda + gk] : zero;
+    }
+  };
+  auto store_a_regs = [&](int st) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int q = tid + c * FAST_THREADS;
+      sA[st][q / FK][q % FK] = areg[c];
+    }
+  };
+
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+
+  // prologue: stage 0
+  if (A_ALIGNED) {
+    load_a_async(0, 0);
+  } else {
+    load_a_regs(0);
+    store_a_regs(0);
+  }
+  load_b(0, 0);
+  cp_async_commit();
+
+  for (int kt = 0; kt < nk; ++kt) {
+    const int st = kt & 1;
+    if (kt + 1 < nk) {
+      if (A_ALIGNED) load_a_async(st ^ 1, (kt + 1) * FK);
+      else load_a_regs((kt + 1) * FK);
+      load_b(st ^ 1, (kt + 1) * FK);
+    }
+    cp_async_commit();
+    cp_async_wait1();  // stage kt has arrived
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < FK; kk += 16) {
+      uint32_t af[4][4], bfr[2][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = wn * 64 + i * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+        ldsm_x4(af[i], &sA[st][r][kk + (lane >> 4) * 8]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        // two adjacent 8-column tiles: lanes 0-15 the first, 16-31 the second
+        const int kr = kk + (lane & 7) + ((lane >> 3) & 1) * 8;
+        const int mc = wm * 32 + jj * 16 + (lane >> 4) * 8;
+        ldsm_x4_t(bfr[jj], &sB[st][kr][mc]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t b[2] = {bfr[j >> 1][(j & 1) * 2], bfr[j >> 1][(j & 1) * 2 + 1]};
+          mma_bf16(acc[i][j], af[i], b);
+        }
+    }
+    if (!A_ALIGNED && kt + 1 < nk) store_a_regs(st ^ 1);
+    __syncthreads();  // stage st is refilled in the next iteration
+  }
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const long long n = n0 + wn * 64 + i * 16 + gid + ((r >= 2) ? 8 : 0);
+        const long long m = m0 + wm * 32 + j * 8 + tig * 2 + (r & 1);
+        if (n >= g.N || m >= g.M) continue;
+        float z = acc[i][j][r];
+        if (g.bias) z += g.bias[n];
+        if (g.mask && !(g.mask[n * g.ldm + m] > 0.0f)) z = 0.0f;
+        if (g.row_scale) z *= g.row_scale[n / g.rows_per_scale];
+        if (g.C) g.C[n * g.ldc + m] = g.accumulate ? g.C[n * g.ldc + m] + z : z;
+        if (g.Cb) g.Cb[n * g.ldcb + m] = __float2bfloat16(g.relu ? fmaxf(z, 0.0f) : z);
+      }
+}
+
 // ---------------------------------------------------------------------------
 // features, targets and statistics
 // ---------------------------------------------------------------------------
@@ -358,6 +530,19 @@ int blocks_for(long long n) {
 }  // namespace
 
 cudaError_t launch_gemm(int amode, int bmode, const GemmArgs& g, cudaStream_t s) {
+  const auto a16 = [](const void* p, long long ld) {
+    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 8 == 0;
+  };
+  if (amode == GEMM_A_NK && bmode == GEMM_B_KM && a16(g.B, g.ldb) &&
+      (g.M + FM - 1) / FM <= 65535) {
+    // N tiles fastest, so the CTAs that share a B tile run together (L2)
+    const dim3 grid((g.N + FN - 1) / FN, (g.M + FM - 1) / FM);
+    if (a16(g.A, g.lda))
+      gemm_bf16_fast_kernel<true><<<grid, FAST_THREADS, 0, s>>>(g);
+    else
+      gemm_bf16_fast_kernel<false><<<grid, FAST_THREADS, 0, s>>>(g);
+    return cudaGetLastError();
+  }
   const dim3 grid((g.M + TM - 1) / TM, (g.N + TN - 1) / TN);
   if (amode == GEMM_A_NK && bmode == GEMM_B_KM)
     gemm_bf16_kernel<GEMM_A_NK, GEMM_B_KM><<<grid, GEMM_THREADS, 0, s>>>(g);

@@ -56,6 +56,31 @@ def test_tensor_core_gemm_all_orientations(abi, amode, bmode):
     assert err < 1e-5, err
 
 
+@pytest.mark.parametrize("K,lda", [(4875, 4875), (264, 264), (100, 104), (37, 40)])
+def test_tensor_core_gemm_pipelined_path(abi, K, lda):
+    """The forward orientation with 16-byte aligned B rows takes the pipelined
+    kernel (128 x 128 tiles, cp.async, ldmatrix); A rows aligned (lda % 8 == 0)
+    or not (the first layer's K = 3 n_v (p+1)^d); ragged N, M, K."""
+    rng = np.random.default_rng(K)
+    N, M, ldb = 300, 1000, 1024
+    A = rng.normal(size=(N, K))
+    B = rng.normal(size=(K, M))
+    Ab, Bb = _bf16(A), _bf16(B)
+    A_ref = Ab.float().numpy().astype(np.float64)
+    B_ref = Bb.float().numpy().astype(np.float64)
+    Ad = torch.zeros((N, lda), dtype=torch.bfloat16)
+    Ad[:, :K] = Ab
+    Bd = torch.zeros((K, ldb), dtype=torch.bfloat16)
+    Bd[:, :M] = Bb
+    Ad, Bd = Ad.cuda(), Bd.cuda()
+    C = torch.full((N, M), float("nan"), dtype=torch.float32, device="cuda")
+    abi.fr_gemm_bf16(0, 0, N, M, K, Ad, lda, Bd, ldb, C, M)
+    torch.cuda.synchronize()
+    ref = A_ref @ B_ref
+    err = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < 3e-5 * max(1.0, np.sqrt(K / 100.0)), err
+
+
 def _history_case(abi, precision=64, n=(5, 4), order=1, steps=4):
     """A small 2-D run with four history levels; returns host copies."""
     d = len(n)
