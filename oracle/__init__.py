@@ -21,6 +21,7 @@ timestep  Classical RK4 pseudo-time step, BDF2 dual time stepping and the
 mlp       Per-element MLP forward/backward/Adam for the learned initial guess
           (no counterpart in the paper).
 
-Parity status (what pins each function) is listed in the module docstrings;
-the only function marked "parity unpinned" is stated there explicitly.
+Parity status: every module's docstring lists what pins it (closed forms,
+textbook operators derived independently with sympy, invariants, brute
+force, planted-mistake tests); no function is left "parity unpinned".
 """
