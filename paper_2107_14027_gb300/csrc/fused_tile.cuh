@@ -1,6 +1,9 @@
-// The volume work of the fused right-hand side for one tile of elements,
-// shared by the RHS kernels (k_fused.cu) and the fused RK4 stage kernels
-// (k_stage.cu).
+// The volume work of the fused right-hand side for one tile of elements
+// (stages 2-6 of Table fr_adv; the method and the work decomposition are
+// described at the top of k_fused.cu), and the fused RHS kernel built on it.
+// Shared by the whole-mesh RHS and the layer sweep (k_fused.cu), the RHS on
+// element ranges for the host-buffer pipeline (k_fused_range.cu) and the
+// fused RK4 stage kernels (k_stage.cu).
 #pragma once
 
 #include "fr_device.cuh"

@@ -1,5 +1,7 @@
 // Fused right-hand-side kernels: stages 2-6 of Table fr_adv in one pass, and
-// the layer sweep that also runs stage 1 in the same persistent kernel.
+// the layer sweep that also runs stage 1 in the same persistent kernel.  The
+// tile work (fused_tile) and the RHS kernel template are in fused_tile.cuh;
+// this file holds the whole-mesh launcher and the sweep.
 //
 // For every element and every axis a the volume work evaluates the normal
 // flux F_a at the solution points (stage 2), the partially corrected
