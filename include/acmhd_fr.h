@@ -69,8 +69,7 @@ enum {
     FR_ECUDA = -2,       /* a CUDA runtime call or kernel launch failed */
     FR_ENOCONV = -3,     /* pseudo-time iteration hit max_iter above tolerance */
     FR_ENONFINITE = -4,  /* a residual norm was NaN or Inf */
-    FR_ENOMEM = -5,      /* device or host allocation failed */
-    FR_ETIMEOUT = -6     /* a bounded in-kernel wait gave up (see fr_check) */
+    FR_ENOMEM = -5       /* device or host allocation failed */
 };
 
 enum { FR_F32 = 32, FR_F64 = 64 };           /* arithmetic precision */
@@ -81,8 +80,7 @@ enum { FR_CORR_DG = 0, FR_CORR_G2 = 1 };     /* correction function (Sec. 2.1) *
 enum {
   FR_SCHEDULE_AUTO = 0,
   FR_SCHEDULE_TWO_KERNELS = 1,
-  FR_SCHEDULE_SWEEP = 2,
-  FR_SCHEDULE_FUSED_STAGE = 3
+  FR_SCHEDULE_FUSED_STAGE = 3     /* (2 is not used) */
 };
 
 /* Create a context.
@@ -109,46 +107,32 @@ int fr_layout(const fr_ctx* ctx, size_t* elem_stride, size_t* n_elem,
               size_t* bytes_per_state);
 
 /* Fused right-hand side R = -div F(U) + S(U) (Table fr_adv stages 1-6):
- * stage 1 stores face traces (only the 1 + 2d variables the normal flux
- * needs); the volume work evaluates the flux (stage 2), the partially
- * corrected divergence (3), the Rusanov/mean common flux (4), the
- * correction (5) and negation plus source (6) per element.
- * Schedules (fr_set_schedule): FR_SCHEDULE_TWO_KERNELS runs a trace kernel
- * and a volume kernel; FR_SCHEDULE_SWEEP runs one persistent kernel that
- * interleaves both per tile of elements, one element layer (z-plane in 3-D,
- * x-row in 2-D) apart, so that U and the traces are reused from L2.  The
- * sweep needs element layers made of whole tiles and at least three layers.
- * On GB300 the in-flight working set of the sweep (about 456 tiles of
- * 32 elements) already fills the 129 MB L2, so it measures no faster than
- * two kernels; FR_SCHEDULE_AUTO (default) runs two kernels.  The sweep's
- * dependency waits are bounded (1 s): a timeout sets the error word read by
- * fr_check.
+ * a trace kernel stores the face traces (stage 1; only the 1 + 2d variables
+ * the normal flux needs), then one volume kernel evaluates per element the
+ * flux (stage 2), the partially corrected divergence (3), the Rusanov/mean
+ * common flux (4), the correction (5) and negation plus source (6).
  * U, R: device state buffers (must not alias).  Uses the context's trace
- * scratch (and, for the sweep, a work queue allocated on first use).
- * Asynchronous on `stream`. */
+ * scratch.  Asynchronous on `stream`. */
 int fr_rhs(fr_ctx* ctx, const void* U, void* R, void* stream);
 
-/* Selects the schedule of fr_rhs, fr_rk_step and fr_pseudo_solve.
- *   FR_SCHEDULE_TWO_KERNELS  fr_rhs: trace kernel + volume kernel; a pseudo
- *                            step adds a separate RK4 update kernel per stage.
- *   FR_SCHEDULE_SWEEP        fr_rhs: the layer sweep (above); separate update.
- *   FR_SCHEDULE_FUSED_STAGE  fr_rk_step / fr_pseudo_solve: one trace kernel
- *                            per call, then each RK4 stage is one kernel: the
- *                            volume work with the stage combination (and the
- *                            FP64 velocity rows, BDF source and residual
- *                            partials of fr_pseudo_solve) in its epilogue,
- *                            writing the face traces of the stage it leaves
- *                            behind; R is never stored.  Same arithmetic in
- *                            the same order as the separate update: identical
- *                            results.  fr_rhs: two kernels.
- *   FR_SCHEDULE_AUTO         (default) two kernels for fr_rhs; for the pseudo
- *                            steps the fused stage at p <= 3, where it is
+/* Selects the schedule of the pseudo steps (fr_rk_step, fr_pseudo_solve).
+ *   FR_SCHEDULE_TWO_KERNELS  each RK4 stage is fr_rhs (trace kernel + volume
+ *                            kernel) followed by a separate update kernel.
+ *   FR_SCHEDULE_FUSED_STAGE  one trace kernel per call, then each RK4 stage
+ *                            is one kernel: the volume work with the stage
+ *                            combination (and the FP64 velocity rows, BDF
+ *                            source and residual partials of fr_pseudo_solve)
+ *                            in its epilogue, writing the face traces of the
+ *                            stage it leaves behind; R is never stored.  Same
+ *                            arithmetic in the same order as the separate
+ *                            update: identical results.
+ *   FR_SCHEDULE_AUTO         (default) the fused stage at p <= 3, where it is
  *                            faster on GB300, the separate update at p >= 4,
  *                            where the volume kernel's occupancy serves the
  *                            update traffic at lower bandwidth than a
  *                            streaming kernel.
- * FR_EINVAL for an unknown schedule, and for FR_SCHEDULE_SWEEP when the mesh
- * does not admit it. */
+ * fr_rhs always runs the trace kernel and the volume kernel.  FR_EINVAL for
+ * an unknown schedule. */
 int fr_set_schedule(fr_ctx* ctx, int schedule);
 
 /* The two halves of fr_rhs, for callers that time or schedule them apart.
@@ -189,26 +173,35 @@ int fr_rk_step(fr_ctx* ctx, void* U, double dtau, void* stream);
 
 /* fr_rhs for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant of fr_rhs with the same kernels
- * and the same results.  Some callers must not allocate device memory once
- * running - e.g. a host application whose own pool allocator reserved the
- * device's memory at start-up, or a time-critical loop in which a device
- * allocation (which can synchronise the whole device) is not allowed - and
- * fr_create allocates.  This call needs no context: it takes the mesh and
- * parameters of fr_create (same meaning and checks) and the state buffers
- * of fr_rhs (same layout; elem_stride = n_elem rounded up to a multiple of
- * 32), and calls no cudaMalloc, cudaFree or other allocating routine.
- * Its face-trace scratch is one fixed 16 MiB array in the library's device
- * image, held by every GPU that loads the library until the process exits.
+ * and the same results, bit for bit.  Some callers must not allocate device
+ * memory once running - e.g. a host application whose own pool allocator
+ * reserved the device's memory at start-up, or a time-critical loop in which
+ * a device allocation (which can synchronise the whole device) is not
+ * allowed - and fr_create allocates.  This call needs no context: it takes
+ * the mesh and parameters of fr_create (same meaning and checks) and the
+ * state buffers of fr_rhs (same layout; elem_stride = n_elem rounded up to a
+ * multiple of 32), and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Its face-trace scratch is one fixed 16 MiB array in the
+ * library's device image, held by every GPU that loads it until the process
+ * exits.
  * Limit: 2d (1+2d) (p+1)^(d-1) * elem_stride * sizeof(value) <= 16 MiB
  * (e.g. 6,240 hexahedra at p = 3 in FP32, 3,104 in FP64); larger problems
  * return FR_EINVAL with the reason in fr_last_error() and launch nothing.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it: make that
- * first call before any stream capture.  All calls share the one array and
- * it keeps the previous call's contents (nothing needs clearing: every
- * entry read is first written by the same call), so calls whose kernels
- * overlap on the GPU - other streams or host threads - race on it and must
- * be serialised by the caller.  Asynchronous on `stream`. */
+ * First call on each device: it looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it.  With
+ * CUDA's default lazy module loading, that lookup and the first launches
+ * also load the library's device code and the 16 MiB array onto the device,
+ * which the driver does by allocating device memory: make one call on each
+ * device before the caller's pool reserves the device's memory (or before
+ * the region that must not allocate, and before any stream capture), or run
+ * with CUDA_MODULE_LOADING=EAGER so that loading happens when the CUDA
+ * context is created.  Later calls allocate nothing.  The cached address
+ * does not survive a reset of the device (cudaDeviceReset) in the process.
+ * All calls share the one array and it keeps the previous call's contents
+ * (nothing needs clearing: every entry read is first written by the same
+ * call), so calls whose kernels overlap on the GPU - other streams or host
+ * threads - race on it and must be serialised by the caller.  Asynchronous
+ * on `stream`. */
 int fr_rhs_static(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
                   double t_r, int precision, int correction, const void* U, void* R,
                   void* stream);
@@ -351,9 +344,8 @@ int fr_mlp_params(fr_mlp* mlp, int which, float* host, size_t count, int set);
 int fr_gemm_bf16(int amode, int bmode, int N, int M, int K, const void* A, long long lda,
                  const void* B, long long ldb, float* C, long long ldc, void* stream);
 
-/* Reads the context's device error word after synchronising `stream`;
- * returns FR_ETIMEOUT if a bounded in-kernel wait gave up since the last
- * call (and clears it), else FR_OK or FR_ECUDA. */
+/* Synchronises `stream` and reports an asynchronous CUDA error (a failed
+ * kernel) as FR_ECUDA with its text in fr_last_error(); FR_OK otherwise. */
 int fr_check(fr_ctx* ctx, void* stream);
 
 /* Static text for a status code. */

@@ -27,7 +27,7 @@ int cuda_status(cudaError_t e, const char* where) {
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 template <typename T>
-void fill_const(const fr_ctx* c, acmhd::FrConst<T>* k) {
+void fill_const_t(const fr_ctx* c, acmhd::FrConst<T>* k) {
   std::memset(k, 0, sizeof(*k));
   const acmhd::Ops1D& o = c->ops;
   for (int a = 0; a < c->dim; ++a) {
@@ -230,54 +230,6 @@ int ensure_unfused(fr_ctx* c) {
 
 bool bad_state_ptr(const void* p) { return p == nullptr || !aligned16(p); }
 
-// The layer sweep needs whole tiles per element layer (a z-plane in 3-D, an
-// x-row in 2-D) and at least three layers.
-void plan_sweep_shape(fr_ctx* c) {
-  const int E = acmhd::fused_tile_elements(c->dim, c->m, c->precision);
-  const long long L = c->dim == 3 ? (long long)c->mesh.n[0] * c->mesh.n[1] : c->mesh.n[0];
-  c->sweep_ok = 0;
-  if (E <= 0 || L % E != 0 || c->ne % E != 0) return;
-  const long long ntiles = c->ne / E, K = L / E;
-  if (ntiles < 2 * K + 1 || ntiles >= (1LL << 29)) return;
-  c->sweep.ntiles = (int)ntiles;
-  c->sweep.K = (int)K;
-  c->sweep_ok = 1;
-}
-
-// Extra distance (in tiles) between a volume unit and the newest trace unit
-// it depends on, so that the trace is usually finished when it is needed:
-// about the number of CTAs resident at once (152 SMs x 3).  Measured on the
-// 64^3 p=3 workload: no extra lag 1.015 ms per RHS (volume units wait on
-// traces claimed just before them), 456 tiles 0.805 ms, all traces first
-// 0.812 ms, the two-kernel schedule 0.80 ms.
-constexpr int kSweepExtraLag = 456;
-
-// Queue: the trace units of the last K tiles; then for i = 0 .. ntiles-1 the
-// trace unit of tile i (unless already queued) followed by the volume unit of
-// tile i - K; then the volume units of the last K tiles.  Every volume unit
-// of tile t comes after the trace units of tiles t-K .. t+K (periodic).
-int ensure_sweep(fr_ctx* c) {
-  if (c->sweep.units) return FR_OK;
-  const int nt = c->sweep.ntiles, K = c->sweep.K;
-  std::vector<int> u;
-  u.reserve(2 * (size_t)nt);
-  for (int t = nt - K; t < nt; ++t) u.push_back(t);
-  const int lag = K + kSweepExtraLag < nt ? K + kSweepExtraLag : nt;
-  for (int i = 0; i < nt; ++i) {
-    if (i < nt - K) u.push_back(i);
-    if (i >= lag) u.push_back((i - lag) | acmhd::kSweepVolume);
-  }
-  for (int t = nt - lag; t < nt; ++t) u.push_back(t | acmhd::kSweepVolume);
-  int st = alloc_zeroed((void**)&c->sweep.units, u.size() * sizeof(int), "sweep plan");
-  if (st == FR_OK) st = alloc_zeroed((void**)&c->sweep.flags, nt * sizeof(unsigned), "sweep plan");
-  if (st == FR_OK) st = alloc_zeroed((void**)&c->sweep.queue, sizeof(unsigned), "sweep plan");
-  if (st == FR_OK)
-    st = cuda_status(cudaMemcpy(c->sweep.units, u.data(), u.size() * sizeof(int),
-                                cudaMemcpyHostToDevice), "sweep plan");
-  c->sweep.nunits = (int)u.size();
-  return st;
-}
-
 size_t vel_doubles(const fr_ctx* c) { return (size_t)c->dim * c->npts * c->stride; }
 
 int ensure_dual(fr_ctx* c) {
@@ -306,6 +258,9 @@ int ensure_history(fr_ctx* c) {
 }
 
 }  // namespace
+
+void acmhd::fill_const(const fr_ctx* c, FrConst<float>* k) { fill_const_t(c, k); }
+void acmhd::fill_const(const fr_ctx* c, FrConst<double>* k) { fill_const_t(c, k); }
 
 void acmhd::set_last_error(const char* msg) {
   std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
@@ -362,9 +317,8 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
     delete c;
     return FR_EINVAL;
   }
-  fill_const<float>(c, &c->cf);
-  fill_const<double>(c, &c->cd);
-  plan_sweep_shape(c);
+  acmhd::fill_const(c, &c->cf);
+  acmhd::fill_const(c, &c->cd);
 
   int st = cuda_status(cudaGetDevice(&c->device), "cudaGetDevice");
   if (st == FR_OK) {
@@ -372,7 +326,6 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
     c->trace_bytes = (size_t)(2 * d) * (1 + 2 * d) * nl * c->stride * c->elem_bytes;
     st = alloc_zeroed(&c->trace, c->trace_bytes, "trace scratch");
   }
-  if (st == FR_OK) st = alloc_zeroed(reinterpret_cast<void**>(&c->err), sizeof(int), "error word");
   if (st != FR_OK) {
     fr_destroy(c);
     return st;
@@ -390,11 +343,11 @@ void fr_destroy(fr_ctx* c) {
   }
   void* bufs[] = {c->trace, c->rk_stage, c->rk_acc, c->rk_k, c->rk_stage2, c->trace2,
                   c->stage_partial, c->unf_uf, c->unf_f,
-                  c->unf_div, c->unf_fi, c->host_u, c->host_r, c->err,
+                  c->unf_div, c->unf_fi, c->host_u, c->host_r,
                   c->dual_vs, c->dual_vacc, c->dual_c, c->dual_partial, c->dual_res, c->dual_v,
                   c->hist_u[0], c->hist_u[1], c->hist_u[2], c->hist_u[3],
                   c->hist_v[0], c->hist_v[1], c->hist_v[2], c->hist_v[3],
-                  c->guess_u, c->guess_v, c->sweep.units, c->sweep.flags, c->sweep.queue};
+                  c->guess_u, c->guess_v};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -411,14 +364,6 @@ int fr_layout(const fr_ctx* c, size_t* elem_stride, size_t* n_elem, size_t* byte
 int fr_rhs(fr_ctx* c, const void* U, void* R, void* stream) {
   if (!c || bad_state_ptr(U) || bad_state_ptr(R) || U == R) return FR_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (c->schedule == FR_SCHEDULE_SWEEP && c->sweep_ok) {
-    int st = ensure_sweep(c);
-    if (st != FR_OK) return st;
-    ++c->sweep_epoch;
-    if (c->sweep_epoch == 0) ++c->sweep_epoch;  // flags start at 0
-    return cuda_status(acmhd::launch_sweep(c, U, c->trace, R, c->sweep, c->sweep_epoch, s),
-                       "sweep kernel");
-  }
   int st = cuda_status(acmhd::launch_trace(c, U, c->trace, s), "trace kernel");
   if (st != FR_OK) return st;
   return cuda_status(acmhd::launch_fused(c, U, c->trace, R, s), "fused kernel");
@@ -427,9 +372,8 @@ int fr_rhs(fr_ctx* c, const void* U, void* R, void* stream) {
 int fr_set_schedule(fr_ctx* c, int schedule) {
   if (!c) return FR_EINVAL;
   if (schedule != FR_SCHEDULE_AUTO && schedule != FR_SCHEDULE_TWO_KERNELS &&
-      schedule != FR_SCHEDULE_SWEEP && schedule != FR_SCHEDULE_FUSED_STAGE)
+      schedule != FR_SCHEDULE_FUSED_STAGE)
     return FR_EINVAL;
-  if (schedule == FR_SCHEDULE_SWEEP && !c->sweep_ok) return FR_EINVAL;
   c->schedule = schedule;
   return FR_OK;
 }
@@ -462,7 +406,7 @@ int fr_rhs_host(fr_ctx* c, const void* U_host, void* R_host, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int bounds[kHostSlabsMax + 1];
   const int S = host_slabs(c, bounds);
-  if (S > 1 && c->schedule != FR_SCHEDULE_SWEEP) {
+  if (S > 1) {
     if ((st = ensure_host_pipeline(c)) != FR_OK) return st;
     st = rhs_host_pipelined(c, U_host, R_host, bounds, S, s);
     if (st == FR_OK) st = cuda_status(cudaStreamSynchronize(s), "stream synchronize");
@@ -771,17 +715,10 @@ int fr_dual_velocity(const fr_ctx* c, double* V, void* stream) {
 
 int fr_check(fr_ctx* c, void* stream) {
   if (!c) return FR_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int flag = 0;
-  int st = cuda_status(cudaMemcpyAsync(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost, s),
-                       "read error word");
-  if (st == FR_OK) st = cuda_status(cudaStreamSynchronize(s), "stream synchronize");
-  if (st != FR_OK) return st;
-  if (flag != 0) {
-    st = cuda_status(cudaMemsetAsync(c->err, 0, sizeof(int), s), "clear error word");
-    return st == FR_OK ? FR_ETIMEOUT : st;
-  }
-  return FR_OK;
+  int st = cuda_status(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)),
+                       "stream synchronize");
+  if (st == FR_OK) st = cuda_status(cudaGetLastError(), "asynchronous error");
+  return st;
 }
 
 const char* fr_strerror(int status) {
@@ -792,7 +729,6 @@ const char* fr_strerror(int status) {
     case FR_ENOCONV: return "pseudo-time iteration did not converge";
     case FR_ENONFINITE: return "non-finite residual";
     case FR_ENOMEM: return "out of memory";
-    case FR_ETIMEOUT: return "bounded in-kernel wait timed out";
     default: return "unknown status";
   }
 }

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "fr_internal.h"
+#include "per_device_once.h"
 
 namespace acmhd {
 
@@ -167,6 +168,18 @@ struct FusedCfg {
   static constexpr int MINB_RAW = SMEM_BLOCKS < REG_BLOCKS ? SMEM_BLOCKS : REG_BLOCKS;
   static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 8 ? 8 : MINB_RAW);
 };
+
+// Raises a kernel's dynamic shared memory limit to `bytes` on the current
+// device, once per device (the attribute is per device context).
+template <class Kernel>
+cudaError_t set_smem_limit(PerDeviceOnce& once, Kernel kern, size_t bytes) {
+  const int st = once.run([](int* d) { return static_cast<int>(cudaGetDevice(d)); },
+                          [&] {
+                            return static_cast<int>(cudaFuncSetAttribute(
+                                kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+                          });
+  return static_cast<cudaError_t>(st);
+}
 
 // x-face exchange between lanes.  The fused kernel keeps E consecutive
 // elements in E consecutive lanes, so the left x-neighbour of element e is

@@ -59,18 +59,6 @@ constexpr int kHostSlabsMax = 4;
 // ring slot of the level `back` steps before the newest one
 inline int hist_slot(int head, int back) { return (head + 4 - back) % 4; }
 
-// Work queue of the layer sweep (device pointers): `units` lists tile
-// indices, trace units plain and volume units with kSweepVolume set.
-constexpr int kSweepVolume = 1 << 30;
-struct SweepPlan {
-  int* units;
-  int nunits;
-  unsigned* flags;   // per tile: epoch of its last finished trace unit
-  int ntiles;
-  int K;             // tiles per element layer: volume(t) needs trace(t-K .. t+K)
-  unsigned* queue;   // next unit to claim
-};
-
 // Arguments of one fused RK4 stage (k_fused.cu, StageOut): the stage input
 // is read by the volume work, its result goes to `next` (stages 0..2) or to
 // U (stage 3), and the traces of that result to `tr`.
@@ -122,7 +110,6 @@ struct fr_ctx {
   cudaStream_t hs[3];  // fr_rhs_host pipeline: copies in, kernels, copies out
   cudaEvent_t hev[2 * acmhd::kHostSlabsMax + 2];  // per slab: in, computed; start; done
   int hs_ready;
-  int* err;            // device error word (bounded waits)
   // dual time stepping (FP64 velocity rows: dim * npts * stride doubles)
   double* dual_vs;     // RK4 stage velocity
   double* dual_vacc;   // RK4 velocity accumulator
@@ -136,13 +123,16 @@ struct fr_ctx {
   int hist_levels;     // number of valid levels (0..4)
   void* guess_u;       // alternative initial guess (state, precision T)
   double* guess_v;     // alternative initial guess (FP64 velocity)
-  int schedule;        // FR_SCHEDULE_* requested for fr_rhs
-  int sweep_ok;        // the mesh admits the layer sweep
-  acmhd::SweepPlan sweep;
-  unsigned sweep_epoch;
+  int schedule;        // FR_SCHEDULE_* requested for the pseudo steps
 };
 
 namespace acmhd {
+
+// The kernel constants of a context: the 1-D operators pre-scaled by the
+// mesh's -J_a, the parameters and the mesh shape (defined in fr_api.cu; used
+// by fr_create and fr_rhs_static alike).
+void fill_const(const fr_ctx* c, FrConst<float>* k);
+void fill_const(const fr_ctx* c, FrConst<double>* k);
 
 // kernel launchers (defined in the k_*.cu files)
 cudaError_t launch_trace(const fr_ctx* c, const void* U, void* trace, cudaStream_t s);
@@ -154,8 +144,6 @@ cudaError_t launch_trace_range(const fr_ctx* c, const void* U, void* trace, int 
 cudaError_t launch_fused_range(const fr_ctx* c, const void* U, const void* trace, void* R,
                                int e_begin, int e_end, cudaStream_t s);
 cudaError_t launch_unfused(const fr_ctx* c, const void* U, void* R, cudaStream_t s);
-cudaError_t launch_sweep(const fr_ctx* c, const void* U, void* Tr, void* R, const SweepPlan& p,
-                         unsigned epoch, cudaStream_t s);
 int fused_tile_elements(int dim, int m, int precision);
 int dual_norm_blocks(const fr_ctx* c);
 cudaError_t launch_sync_velocity(const fr_ctx* c, const double* V, void* U, cudaStream_t s);

@@ -15,6 +15,15 @@
 // the previous call's contents: nothing needs clearing, because the trace
 // kernel writes every entry that the fused kernel then reads, but calls whose
 // kernels overlap on the GPU (other streams, other host threads) race on it.
+//
+// The library is linked without relocatable device code, so this file is a
+// module of its own.  Under CUDA's default lazy module loading the module -
+// the array included - is loaded onto a device at the first
+// cudaGetSymbolAddress or launch that needs it, and loading allocates device
+// memory.  So the first call on each device may allocate (and fail with
+// FR_ECUDA when the device's memory is already taken); later calls do not.
+// Callers make that first call before their pool reserves memory, or set
+// CUDA_MODULE_LOADING=EAGER.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,7 +45,8 @@ std::mutex g_static_mu;
 void* g_static_addr[kMaxDevices] = {};
 
 // Device address of g_static_trace on the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  The cache is not
+// invalidated by a device reset.
 cudaError_t static_trace_address(int device, void** out) {
   std::lock_guard<std::mutex> lock(g_static_mu);
   if (!g_static_addr[device]) {
@@ -47,36 +57,6 @@ cudaError_t static_trace_address(int device, void** out) {
   }
   *out = g_static_addr[device];
   return cudaSuccess;
-}
-
-template <typename T>
-void static_const(const fr_ctx& c, acmhd::FrConst<T>* k) {
-  std::memset(k, 0, sizeof(*k));
-  const acmhd::Ops1D& o = c.ops;
-  for (int a = 0; a < c.dim; ++a) {
-    const double J = 2.0 / ((c.mesh.hi[a] - c.mesh.lo[a]) / c.mesh.n[a]);
-    k->J[a] = static_cast<T>(J);
-    for (int i = 0; i < o.m; ++i) {
-      for (int q = 0; q < o.m; ++q) k->A[a][i][q] = static_cast<T>(-J * o.Dt[i][q]);
-      k->bl[a][i] = static_cast<T>(-J * o.dhl[i]);
-      k->br[a][i] = static_cast<T>(-J * o.dhr[i]);
-    }
-  }
-  for (int i = 0; i < o.m; ++i) {
-    for (int q = 0; q < o.m; ++q) k->Dt[i][q] = static_cast<T>(o.Dt[i][q]);
-    k->dhl[i] = static_cast<T>(o.dhl[i]);
-    k->dhr[i] = static_cast<T>(o.dhr[i]);
-    k->lm[i] = static_cast<T>(o.lm[i]);
-    k->lp[i] = static_cast<T>(o.lp[i]);
-  }
-  k->zeta = static_cast<T>(c.zeta);
-  k->nu = static_cast<T>(c.nu);
-  k->inv_t = static_cast<T>(1.0 / c.t_r);
-  k->n[0] = c.mesh.n[0];
-  k->n[1] = c.mesh.n[1];
-  k->n[2] = c.dim == 3 ? c.mesh.n[2] : 1;
-  k->ne = c.ne;
-  k->stride = static_cast<int>(c.stride);
 }
 
 int static_fail(int status, const char* msg) {
@@ -141,9 +121,9 @@ extern "C" int fr_rhs_static(const fr_mesh* mesh, int order, int nvars, double z
   if (!acmhd::build_ops1d(order, correction, &c.ops))
     return static_fail(FR_EINVAL, "operator construction failed");
   if (precision == FR_F32)
-    static_const<float>(c, &c.cf);
+    acmhd::fill_const(&c, &c.cf);
   else
-    static_const<double>(c, &c.cd);
+    acmhd::fill_const(&c, &c.cd);
 
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);

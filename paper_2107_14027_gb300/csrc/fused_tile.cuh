@@ -1,21 +1,14 @@
 // The volume work of the fused right-hand side for one tile of elements
 // (stages 2-6 of Table fr_adv; the method and the work decomposition are
 // described at the top of k_fused.cu), and the fused RHS kernel built on it.
-// Shared by the whole-mesh RHS and the layer sweep (k_fused.cu), the RHS on
-// element ranges for the host-buffer pipeline (k_fused_range.cu) and the
-// fused RK4 stage kernels (k_stage.cu).
+// Shared by the whole-mesh RHS (k_fused.cu), the RHS on element ranges for
+// the host-buffer pipeline (k_fused_range.cu) and the fused RK4 stage
+// kernels (k_stage.cu).
 #pragma once
 
 #include "fr_device.cuh"
 
 namespace acmhd {
-
-// traces are read through L2 only when other CTAs of the same kernel write them
-template <bool COHERENT, typename T>
-__device__ __forceinline__ T ld_trace(const T* p) {
-  if (COHERENT) return __ldcg(p);
-  return __ldg(p);
-}
 
 // Output policies of the volume work.  Every entry i of R is produced
 // exactly once and handed over as out.store(i, value, pre), which returns the
@@ -134,7 +127,7 @@ struct StageOut {
 // entries, and their traces on all faces are taken from sA.  Traces go to
 // out.tr (layout of the trace kernel, x faces only where the lane exchange
 // cannot serve them).
-template <int D, int M, typename T, int E, int NW, bool COHERENT, class Out>
+template <int D, int M, typename T, int E, int NW, class Out>
 __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __restrict__ Tr,
                                            Out& out, const FrConst<T>& c, int e0, T* sU,
                                            T* sA) {
@@ -180,10 +173,10 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
       T nb_lo[NS], nb_hi[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        nb_lo[s] = lo_mem ? ld_trace<COHERENT>(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S +
+        nb_lo[s] = lo_mem ? __ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S +
                                                nb[a][0])
                           : T(0);
-        nb_hi[s] = hi_mem ? ld_trace<COHERENT>(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S +
+        nb_hi[s] = hi_mem ? __ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S +
                                                nb[a][1])
                           : T(0);
       }
@@ -341,7 +334,7 @@ fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ 
   T* sA = sU + (1 + D) * NP * E;           // [1+D][NP][E]
   RhsOut<T> out{R};
   const int tile = RANGED ? tile0 + (int)blockIdx.x : (int)blockIdx.x;
-  fused_tile<D, M, T, E, NW, false>(U, Tr, out, c, tile * E, sU, sA);
+  fused_tile<D, M, T, E, NW>(U, Tr, out, c, tile * E, sU, sA);
 }
 
 // elements [e_begin, e_end); e_begin a multiple of 32 (and so of E), and 0
@@ -351,13 +344,9 @@ cudaError_t fused_launch(const FrConst<T>& c, const void* U, const void* Tr, voi
                          int e_end, cudaStream_t s) {
   using C = FusedCfg<D, M, T>;
   auto kern = fused_kernel<D, M, T, C::E, C::NW, C::MINB, RANGED>;
-  static bool attr_done = false;  // per template instance
-  if (!attr_done) {
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::SMEM);
-    if (err != cudaSuccess) return err;
-    attr_done = true;
-  }
+  static PerDeviceOnce smem_once;  // per template instance
+  cudaError_t err = set_smem_limit(smem_once, kern, C::SMEM);
+  if (err != cudaSuccess) return err;
   const int nblk = (e_end - e_begin + C::E - 1) / C::E;
   if (nblk <= 0) return cudaSuccess;
   kern<<<nblk, C::NW * 32, C::SMEM, s>>>(static_cast<const T*>(U), static_cast<const T*>(Tr),

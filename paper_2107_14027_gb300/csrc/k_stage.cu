@@ -18,7 +18,7 @@ stage_kernel(const T* __restrict__ U, const T* __restrict__ Tr, StageOut<T> o,
   T* sA = sU + (1 + D) * NP * E;
   __shared__ double s_red[NW];
   o.sq = 0.0;
-  fused_tile<D, M, T, E, NW, false>(U, Tr, o, c, blockIdx.x * E, sU, sA);
+  fused_tile<D, M, T, E, NW>(U, Tr, o, c, blockIdx.x * E, sU, sA);
   if (o.dual && o.stage == 0) {
     // fixed-order block sum: warp tree, then the warps in order
     double v = o.sq;
@@ -39,13 +39,9 @@ cudaError_t stage_launch(const fr_ctx* ctx, const FrConst<T>& c, const void* U, 
                          const StageArgs& a, double* partial, cudaStream_t s) {
   using C = FusedCfg<D, M, T>;
   auto kern = stage_kernel<D, M, T, C::E, C::NW, C::MINB>;
-  static bool attr_done = false;  // per template instance
-  if (!attr_done) {
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::SMEM);
-    if (err != cudaSuccess) return err;
-    attr_done = true;
-  }
+  static PerDeviceOnce smem_once;  // per template instance
+  cudaError_t err = set_smem_limit(smem_once, kern, C::SMEM);
+  if (err != cudaSuccess) return err;
   StageOut<T> o;
   o.U = static_cast<T*>(a.U);
   o.next = static_cast<T*>(a.next);

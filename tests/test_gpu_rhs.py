@@ -231,47 +231,3 @@ def test_invalid_arguments_are_rejected(abi):
         abi.fr_check(ctx)
     finally:
         abi.fr_destroy(ctx)
-
-
-# meshes whose element layers are whole tiles (the layer sweep applies)
-SWEEP_CASES = [((32, 2, 8), 3, 32), ((16, 3, 6), 3, 64), ((32, 5), 2, 32), ((16, 2, 4), 5, 32),
-               ((8, 3, 3), 6, 32), ((32, 3, 4), 1, 64), ((64, 4), 4, 64)]
-
-
-@pytest.mark.parametrize("n,order,precision", SWEEP_CASES)
-def test_sweep_schedule_matches_oracle_and_two_kernels(abi, n, order, precision):
-    d = len(n)
-    nv = 1 + d + d * d
-    U, mesh, prm, lo, hi = parity.make_case(n, order)
-    ctx = abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, precision, 0)
-    try:
-        abi.fr_set_schedule(ctx, abi.FR_SCHEDULE_SWEEP)
-        Ud = abi.pack_state(ctx, U, precision)
-        R_sweep = abi.new_state(ctx, precision, fill=float("nan"))
-        R_two = abi.new_state(ctx, precision, fill=float("nan"))
-        for _ in range(3):                       # epochs advance between calls
-            abi.fr_rhs(ctx, Ud, R_sweep)
-        abi.fr_set_schedule(ctx, abi.FR_SCHEDULE_TWO_KERNELS)
-        abi.fr_rhs(ctx, Ud, R_two)
-        torch.cuda.synchronize()
-        abi.fr_check(ctx)                        # no bounded wait timed out
-        stride, ne, _ = abi.fr_layout(ctx)
-        assert torch.equal(R_sweep[:, :ne], R_two[:, :ne])
-        R = abi.unpack_state(ctx, R_sweep, nv)
-        U_used = abi.unpack_state(ctx, Ud, nv)
-    finally:
-        abi.fr_destroy(ctx)
-    R_ref = fr.rhs(U_used, mesh, order, prm)
-    scale = parity.term_scale(U_used, mesh, order, prm)
-    parity.assert_parity(R, R_ref, scale, precision, plain=True, label=f"sweep {n} p={order}")
-
-
-def test_sweep_is_refused_where_it_does_not_apply(abi):
-    ctx = abi.fr_create((9, 8, 7), (0,) * 3, (1,) * 3, 3, 13, 2.5, 1e-3, 5e-3, 32, 0)
-    try:
-        with pytest.raises(abi.FrError) as ei:
-            abi.fr_set_schedule(ctx, abi.FR_SCHEDULE_SWEEP)
-        assert ei.value.status == abi.FR_EINVAL
-        abi.fr_set_schedule(ctx, abi.FR_SCHEDULE_AUTO)   # falls back to two kernels
-    finally:
-        abi.fr_destroy(ctx)
