@@ -23,7 +23,12 @@ Pins (tests/test_oracle_fr.py): the discrete RHS converges to the textbook
 continuous operators (Chorin's -zeta div V, incompressible Navier-Stokes
 momentum, relaxation (grad u - q)/T) computed independently with sympy; the
 count of structurally non-zero flux entries equals the paper's sparsity
-formula; Rusanov consistency F^I(U, U) = F(U) and energy dissipation.
+formula; the eigenvalues of the flux Jacobian's (P, V) block are Chorin's
+V_a, V_a +- sqrt(V_a^2 + zeta); the Rusanov dissipation coefficient
+-2 dF^I_P/dP_R equals the larger of the two sides' spectral radii of that
+Jacobian (numpy eigenvalues); Rusanov consistency F^I(U, U) = F(U) and
+energy dissipation.  tests/test_oracle_mms.py: the steady manufactured
+solution is reached at order p + 1 in the velocity.
 """
 import numpy as np
 

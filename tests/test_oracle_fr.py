@@ -276,3 +276,79 @@ def test_dense_matches_sum_factorised(d, p, corr):
     # the per-element sampler returns the same columns
     Rs = fr.rhs_dense(U, mesh, p, prm, corr, elems=[mesh.ne - 1, 0])
     np.testing.assert_allclose(Rs, R[:, :, [mesh.ne - 1, 0]], rtol=0, atol=1e-12 * np.abs(R).max())
+
+
+# ---------------------------------------------------------------------------
+# Rusanov wave speed = spectral radius of the ACM flux Jacobian
+# ---------------------------------------------------------------------------
+
+def _acm_spectral_radius(U, a, zeta):
+    """Largest |eigenvalue| of dF_a/dU restricted to the hyperbolic (P, V)
+    block, from numpy's eigenvalue routine applied to the Jacobian of the
+    oracle's flux (central differences; the flux is quadratic, so they are
+    exact up to rounding).  nu = 0: the viscous part is not hyperbolic."""
+    d = {7: 2, 13: 3}[U.shape[0]]
+    k = 1 + d
+    A = np.zeros((k, k))
+    h = 1e-3
+    for j in range(k):
+        Up, Um = U.copy(), U.copy()
+        Up[j] += h
+        Um[j] -= h
+        A[:, j] = (acmhd.flux(Up, a, zeta, 0.0, 1.0)[:k] - acmhd.flux(Um, a, zeta, 0.0, 1.0)[:k]) / (2 * h)
+    return np.abs(np.linalg.eigvals(A)).max()
+
+
+def _rusanov_speed_is_spectral_radius(seed=2):
+    """The dissipation coefficient of the common flux on the P equation,
+    s = -2 dF^I_P / dP_R, equals max(rho(U_L), rho(U_R)), rho the spectral
+    radius of the ACM flux Jacobian (Sec. 5: a Rusanov solver for the
+    hyperbolic part)."""
+    rng = np.random.default_rng(seed)
+    ok = True
+    for d in (2, 3):
+        nv = acmhd.nvars(d)
+        for trial in range(6):
+            UL = rng.normal(size=(nv, 1)) * 1.5
+            UR = rng.normal(size=(nv, 1)) * 1.5
+            zeta = float(rng.uniform(0.5, 3.0))
+            for a in range(d):
+                h = 1e-3
+                Rp, Rm = UR.copy(), UR.copy()
+                Rp[0] += h
+                Rm[0] -= h
+                dF = (acmhd.common_flux(UL, Rp, a, zeta, 0.1, 0.3)[0]
+                      - acmhd.common_flux(UL, Rm, a, zeta, 0.1, 0.3)[0]) / (2 * h)
+                s = -2.0 * float(dF[0])
+                rho = max(_acm_spectral_radius(UL[:, 0], a, zeta),
+                          _acm_spectral_radius(UR[:, 0], a, zeta))
+                ok &= abs(s - rho) <= 1e-9 * rho
+    return bool(ok)
+
+
+def test_rusanov_speed_is_the_acm_spectral_radius():
+    assert _rusanov_speed_is_spectral_radius()
+
+
+def test_acm_eigenvalues_closed_form():
+    """The eigenvalues of the ACM flux Jacobian in direction a are V_a and
+    V_a +- sqrt(V_a^2 + zeta) (Chorin's artificial compressibility): checked
+    against numpy's eigenvalues of the oracle's flux Jacobian."""
+    rng = np.random.default_rng(5)
+    for d in (2, 3):
+        U = rng.normal(size=acmhd.nvars(d))
+        zeta = 1.7
+        for a in range(d):
+            k = 1 + d
+            A = np.zeros((k, k))
+            for j in range(k):
+                Up, Um = U.copy(), U.copy()
+                Up[j] += 1e-3
+                Um[j] -= 1e-3
+                A[:, j] = (acmhd.flux(Up, a, zeta, 0.0, 1.0)[:k]
+                           - acmhd.flux(Um, a, zeta, 0.0, 1.0)[:k]) / 2e-3
+            lam = np.sort(np.linalg.eigvals(A).real)
+            va = U[1 + a]
+            c = np.sqrt(va * va + zeta)
+            expect = np.sort([va - c] + [va] * (d - 1) + [va + c])
+            np.testing.assert_allclose(lam, expect, rtol=0, atol=1e-9)

@@ -3,14 +3,17 @@
 Each case plants one mistake in the oracle (on the CPU, by monkeypatching)
 and checks that at least one of the independent pins of
 tests/test_oracle_fr.py fails: convergence to the sympy continuous
-operators, discrete conservation, acoustic energy dissipation, or agreement
-of the sum-factorised and dense paths.
+operators, discrete conservation, acoustic energy dissipation, agreement
+of the sum-factorised and dense paths, or the Rusanov speed against the
+spectral radius of the flux Jacobian.  (The manufactured-solution pin has
+its own planted mistake in tests/test_oracle_mms.py.)
 """
 import numpy as np
 import pytest
 
 from oracle import acmhd, fr, ops1d
-from tests.test_oracle_fr import _continuous_case, _rand_state, _sample, _weights
+from tests.test_oracle_fr import (_continuous_case, _rand_state, _rusanov_speed_is_spectral_radius,
+                                  _sample, _weights)
 
 
 def _converges(d=2, p=2, ns=(8, 16), with_offset=True):
@@ -58,7 +61,8 @@ def _dense_agrees(d=2, p=2):
 
 
 def _all_pins_pass():
-    return _converges() and _conserves() and _dissipates() and _dense_agrees()
+    return (_converges() and _conserves() and _dissipates() and _dense_agrees()
+            and _rusanov_speed_is_spectral_radius())
 
 
 def test_unmutated_oracle_passes_all_pins():
@@ -68,6 +72,7 @@ def test_unmutated_oracle_passes_all_pins():
 _orig_flux = acmhd.flux
 _orig_common = acmhd.common_flux
 _orig_init = ops1d.Ops1D.__init__
+_orig_speed = acmhd.wave_speed
 
 
 def _flux_nu_sign(U, a, zeta, nu, T):
@@ -104,6 +109,23 @@ def _common_one_sided(UL, UR, a, zeta, nu, T):
     return _orig_flux(UL, a, zeta, nu, T)
 
 
+def _speed_sqrt_zeta(U, a, zeta):
+    return np.sqrt(zeta) * np.ones_like(U[0])
+
+
+def _speed_plus_zeta(U, a, zeta):
+    return np.abs(U[1 + a]) + zeta
+
+
+def _common_min_speed(UL, UR, a, zeta, nu, T):
+    """Rusanov with the smaller of the two sides' speeds."""
+    d = {7: 2, 13: 3}[UL.shape[0]]
+    FI = 0.5 * (_orig_flux(UL, a, zeta, nu, T) + _orig_flux(UR, a, zeta, nu, T))
+    s = np.minimum(_orig_speed(UL, a, zeta), _orig_speed(UR, a, zeta))
+    FI[: 1 + d] -= 0.5 * s * (UR[: 1 + d] - UL[: 1 + d])
+    return FI
+
+
 def _ops_mutator(kind):
     def init(self, order, correction="dg"):
         _orig_init(self, order, correction)
@@ -136,6 +158,9 @@ MUTATIONS = {
     "source_sign": lambda mp: mp.setattr(acmhd, "source", _source_sign),
     "anti_dissipative": lambda mp: mp.setattr(acmhd, "common_flux", _common_anti_dissipative),
     "one_sided_flux": lambda mp: mp.setattr(acmhd, "common_flux", _common_one_sided),
+    "speed_sqrt_zeta": lambda mp: mp.setattr(acmhd, "wave_speed", _speed_sqrt_zeta),
+    "speed_plus_zeta": lambda mp: mp.setattr(acmhd, "wave_speed", _speed_plus_zeta),
+    "speed_min_of_sides": lambda mp: mp.setattr(acmhd, "common_flux", _common_min_speed),
     "D_transposed": lambda mp: mp.setattr(ops1d.Ops1D, "__init__", _ops_mutator("D_transposed")),
     "corrections_swapped": lambda mp: mp.setattr(ops1d.Ops1D, "__init__", _ops_mutator("corrections_swapped")),
     "ends_swapped": lambda mp: mp.setattr(ops1d.Ops1D, "__init__", _ops_mutator("ends_swapped")),
