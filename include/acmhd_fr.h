@@ -337,6 +337,24 @@ int fr_mlp_predict(fr_mlp* mlp, void* U, double* V, void* stream);
 int fr_mlp_predict_for(fr_mlp* mlp, fr_ctx* ctx, void* U, double* V, void* stream);
 int fr_mlp_params(fr_mlp* mlp, int which, float* host, size_t count, int set);
 
+/* One full-batch Adam step over the collected samples (fr_mlp_train with
+ * one epoch); *loss (if non-NULL) is the loss before the step.  Synchronises
+ * `stream`. */
+int fr_mlp_train_step(fr_mlp* mlp, double lr, double* loss, void* stream);
+
+/* Save / load a network.  The file holds a magic word, a format version, the
+ * discretization it was built for (dimension, order, variables, points per
+ * element), its sizes, the Adam step count, the feature and output scales,
+ * the FP32 master weights and Adam's moments, and a checksum (FNV-1a 64 over
+ * all preceding bytes); little-endian.  fr_mlp_load creates a network bound
+ * to ctx with room for `capacity` samples and restores all of that, so
+ * predictions are bit-identical to the saved network's and training resumes
+ * where it stopped.  The collected samples are not saved.  FR_EINVAL (reason
+ * in fr_last_error) for a missing, corrupt or foreign file, or a network of
+ * another discretization (dimension, order or variable count). */
+int fr_mlp_save(const fr_mlp* mlp, const char* path);
+int fr_mlp_load(fr_ctx* ctx, const char* path, int capacity, fr_mlp** out);
+
 /* The tensor-core GEMM of the MLP as a utility: C[N x M] = A . B in FP32
  * from BF16 operands.  amode 0: A[n * lda + k]; 1: A[k * lda + n].
  * bmode 0: B[k * ldb + m]; 1: B[m * ldb + k].  C[n * ldc + m].  Device

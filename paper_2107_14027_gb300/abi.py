@@ -26,7 +26,8 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", 
            "fr_rk_step", "fr_check", "fr_strerror", "fr_last_error", "fr_rhs_static",
            "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity", "fr_dual_copy",
            "fr_mlp_create", "fr_mlp_destroy", "fr_mlp_info", "fr_mlp_collect", "fr_mlp_loss_grad",
-           "fr_mlp_train", "fr_mlp_predict", "fr_mlp_predict_for", "fr_mlp_params", "fr_gemm_bf16"]
+           "fr_mlp_train", "fr_mlp_predict", "fr_mlp_predict_for", "fr_mlp_params", "fr_gemm_bf16",
+           "fr_mlp_train_step", "fr_mlp_save", "fr_mlp_load"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -97,6 +98,9 @@ def _lib():
         lib.fr_mlp_predict.argtypes = [vp, vp, vp, vp]
         lib.fr_mlp_predict_for.argtypes = [vp, vp, vp, vp, vp]
         lib.fr_mlp_params.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float), sz, i32]
+        lib.fr_mlp_train_step.argtypes = [vp, dbl, dp, vp]
+        lib.fr_mlp_save.argtypes = [vp, ctypes.c_char_p]
+        lib.fr_mlp_load.argtypes = [vp, ctypes.c_char_p, i32, ctypes.POINTER(vp)]
         lib.fr_gemm_bf16.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.c_longlong, vp,
                                      ctypes.c_longlong, vp, ctypes.c_longlong, vp]
         lib.fr_strerror.argtypes = [i32]
@@ -318,6 +322,24 @@ def fr_mlp_train(mlp, epochs, lr, stream=None):
     _check(_lib().fr_mlp_train(ctypes.c_void_p(mlp), int(epochs), float(lr), ctypes.byref(loss),
                                _stream(stream)), "fr_mlp_train")
     return loss.value
+
+
+def fr_mlp_train_step(mlp, lr, stream=None):
+    loss = ctypes.c_double()
+    _check(_lib().fr_mlp_train_step(ctypes.c_void_p(mlp), float(lr), ctypes.byref(loss),
+                                    _stream(stream)), "fr_mlp_train_step")
+    return loss.value
+
+
+def fr_mlp_save(mlp, path):
+    _check(_lib().fr_mlp_save(ctypes.c_void_p(mlp), os.fsencode(path)), "fr_mlp_save")
+
+
+def fr_mlp_load(ctx, path, capacity=1):
+    out = ctypes.c_void_p()
+    _check(_lib().fr_mlp_load(ctypes.c_void_p(ctx), os.fsencode(path), int(capacity),
+                              ctypes.byref(out)), "fr_mlp_load")
+    return out.value
 
 
 def fr_mlp_predict(mlp, U, V, stream=None):

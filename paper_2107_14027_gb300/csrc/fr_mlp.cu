@@ -500,6 +500,136 @@ int fr_mlp_predict_for(fr_mlp* q, fr_ctx* c, void* U, double* V, void* stream) {
   return st;
 }
 
+int fr_mlp_train_step(fr_mlp* q, double lr, double* loss, void* stream) {
+  return fr_mlp_train(q, 1, lr, loss, stream);
+}
+
+// Network file (little-endian):
+//   char[8] "ACMHDMLP", uint32 version (1), int32 dim, order, nv, npts, K, H,
+//   NO, adam_t, scales_set; float in_scale[3 nv], out_scale[nv]; then for
+//   each of W1 b1 W2 b2 W3 b3 the FP32 master values, then the same blocks of
+//   Adam's first and second moments; uint64 FNV-1a hash of everything before.
+namespace {
+constexpr char kMlpMagic[8] = {'A', 'C', 'M', 'H', 'D', 'M', 'L', 'P'};
+constexpr uint32_t kMlpVersion = 1;
+
+struct MlpFile {
+  std::vector<unsigned char> bytes;
+  void put(const void* p, size_t n) {
+    const auto* c = static_cast<const unsigned char*>(p);
+    bytes.insert(bytes.end(), c, c + n);
+  }
+};
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+int mlp_fail(int st, const char* msg) {
+  acmhd::set_last_error(msg);
+  return st;
+}
+}  // namespace
+
+int fr_mlp_save(const fr_mlp* q, const char* path) {
+  if (!q || !path) return FR_EINVAL;
+  const fr_ctx* c = q->ctx;
+  MlpFile f;
+  f.put(kMlpMagic, 8);
+  f.put(&kMlpVersion, 4);
+  const int32_t hdr[9] = {c->dim, c->order, c->nv, c->npts, q->K, q->H, q->NO, q->adam_t,
+                          q->scales_set};
+  f.put(hdr, sizeof(hdr));
+  std::vector<float> sc(4 * (size_t)c->nv);
+  int st = st_of(cudaMemcpy(sc.data(), q->in_scale, 3 * c->nv * 4, cudaMemcpyDeviceToHost), "save");
+  if (!st) st = st_of(cudaMemcpy(sc.data() + 3 * c->nv, q->out_scale, c->nv * 4, cudaMemcpyDeviceToHost),
+                      "save");
+  if (st) return st;
+  f.put(sc.data(), sc.size() * 4);
+  for (float* const* arr : {q->p, q->m, q->v}) {
+    for (int i = 0; i < 6; ++i) {
+      std::vector<float> h(q->cnt[i]);
+      if ((st = st_of(cudaMemcpy(h.data(), arr[i], q->cnt[i] * 4, cudaMemcpyDeviceToHost), "save")))
+        return st;
+      f.put(h.data(), h.size() * 4);
+    }
+  }
+  const uint64_t hash = fnv1a(f.bytes.data(), f.bytes.size());
+  f.put(&hash, 8);
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return mlp_fail(FR_EINVAL, "fr_mlp_save: cannot open the file for writing");
+  const size_t w = std::fwrite(f.bytes.data(), 1, f.bytes.size(), fp);
+  const int closed = std::fclose(fp);
+  if (w != f.bytes.size() || closed != 0) return mlp_fail(FR_EINVAL, "fr_mlp_save: write failed");
+  return FR_OK;
+}
+
+int fr_mlp_load(fr_ctx* c, const char* path, int capacity, fr_mlp** out) {
+  if (!c || !path || !out) return FR_EINVAL;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return mlp_fail(FR_EINVAL, "fr_mlp_load: cannot open the file");
+  std::vector<unsigned char> b;
+  unsigned char buf[1 << 16];
+  size_t r;
+  while ((r = std::fread(buf, 1, sizeof(buf), fp)) > 0) b.insert(b.end(), buf, buf + r);
+  std::fclose(fp);
+  const size_t head = 8 + 4 + 9 * 4;
+  if (b.size() < head + 8 || std::memcmp(b.data(), kMlpMagic, 8) != 0)
+    return mlp_fail(FR_EINVAL, "fr_mlp_load: not a network file");
+  uint32_t ver;
+  std::memcpy(&ver, b.data() + 8, 4);
+  if (ver != kMlpVersion) return mlp_fail(FR_EINVAL, "fr_mlp_load: unsupported file version");
+  uint64_t hash;
+  std::memcpy(&hash, b.data() + b.size() - 8, 8);
+  if (fnv1a(b.data(), b.size() - 8) != hash)
+    return mlp_fail(FR_EINVAL, "fr_mlp_load: checksum mismatch (corrupt file)");
+  int32_t hdr[9];
+  std::memcpy(hdr, b.data() + 12, sizeof(hdr));
+  const int dim = hdr[0], order = hdr[1], nv = hdr[2], npts = hdr[3], K = hdr[4], H = hdr[5],
+            NO = hdr[6];
+  if (dim != c->dim || order != c->order || nv != c->nv || npts != c->npts || NO != nv * npts ||
+      K != 3 * NO)
+    return mlp_fail(FR_EINVAL, "fr_mlp_load: the network belongs to another discretization");
+  const size_t cnt[6] = {(size_t)H * K, (size_t)H, (size_t)H * H, (size_t)H, (size_t)NO * H,
+                         (size_t)NO};
+  size_t total = 0;
+  for (size_t x : cnt) total += x;
+  if (H < 8 || H > 4096 || b.size() != head + 4 * (4 * (size_t)nv + 3 * total) + 8)
+    return mlp_fail(FR_EINVAL, "fr_mlp_load: file size does not match its header");
+  fr_mlp* q = nullptr;
+  int st = fr_mlp_create(c, H, capacity, 0, &q);
+  if (st != FR_OK) return st;
+  const unsigned char* p = b.data() + head;
+  std::vector<float> sc(4 * (size_t)nv), inv(4 * (size_t)nv);
+  std::memcpy(sc.data(), p, sc.size() * 4);
+  p += sc.size() * 4;
+  for (size_t i = 0; i < sc.size(); ++i) inv[i] = sc[i] > 0.0f ? 1.0f / sc[i] : 1.0f;
+  st = st_of(cudaMemcpy(q->in_scale, sc.data(), 3 * nv * 4, cudaMemcpyHostToDevice), "load");
+  if (!st) st = st_of(cudaMemcpy(q->in_scale_inv, inv.data(), 3 * nv * 4, cudaMemcpyHostToDevice), "load");
+  if (!st) st = st_of(cudaMemcpy(q->out_scale, sc.data() + 3 * nv, nv * 4, cudaMemcpyHostToDevice), "load");
+  if (!st)
+    st = st_of(cudaMemcpy(q->out_scale_inv, inv.data() + 3 * nv, nv * 4, cudaMemcpyHostToDevice), "load");
+  float** dst[3] = {q->p, q->m, q->v};
+  for (int a = 0; a < 3 && !st; ++a) {
+    for (int i = 0; i < 6 && !st; ++i) {
+      st = st_of(cudaMemcpy(dst[a][i], p, cnt[i] * 4, cudaMemcpyHostToDevice), "load");
+      p += cnt[i] * 4;
+      if (!st && a == 0) st = st_of(acmhd::launch_to_bf16(cnt[i], q->p[i], q->pb[i], 0), "load");
+    }
+  }
+  if (!st) st = st_of(cudaDeviceSynchronize(), "load");
+  if (st) {
+    fr_mlp_destroy(q);
+    return st;
+  }
+  q->adam_t = hdr[7];
+  q->scales_set = hdr[8];
+  *out = q;
+  return FR_OK;
+}
+
 int fr_gemm_bf16(int amode, int bmode, int N, int M, int K, const void* A, long long lda,
                  const void* B, long long ldb, float* C, long long ldc, void* stream) {
   if (N < 1 || M < 1 || K < 1 || !A || !B || !C || (amode != 0 && amode != 1) ||

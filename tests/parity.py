@@ -11,8 +11,11 @@ to the result, so the parity bound for variable v is
 
 with tol = 1e-12 (FP64) and 2e-5 (FP32), the oracle evaluated in FP64 on
 the identical (already rounded) input values.  Where the result does not
-cancel (noisy inputs) FP64 must also meet the plain relative bound
-|| dR_v || <= 1e-12 || R_oracle,v ||.
+cancel, the plain relative bound || dR_v || <= tol || R_oracle,v || must
+hold as well: in FP64 for every variable whose || R_v || / || B_v || exceeds
+1e-3, and in FP32 for the P and V rows under the same condition (the
+auxiliary rows' result (grad u - q)/T cancels by up to 1e5 against its
+terms, so their plain FP32 error is reported, not bounded).
 """
 import numpy as np
 
@@ -21,7 +24,8 @@ from oracle.ops1d import Ops1D
 from paper_2107_14027_gb300 import workloads as W
 
 TOL = {32: 2e-5, 64: 1e-12}
-PLAIN_TOL_F64 = 1e-12
+PLAIN_TOL = {32: 2e-5, 64: 1e-12}
+CANCEL_MIN = 1e-3
 
 
 def term_scale(U, mesh, order, prm, corr="dg"):
@@ -50,14 +54,22 @@ def errors(R_gpu, R_ref, scale):
     return scaled, diff / np.maximum(ref, 1e-300), ref / safe
 
 
-def assert_parity(R_gpu, R_ref, scale, precision, plain=False, label=""):
+def assert_parity(R_gpu, R_ref, scale, precision, plain=False, label="", dim=None):
+    """Scaled bound on every variable; with `plain`, the plain relative bound
+    on the variables whose result does not cancel (FP64: all rows; FP32: the
+    P and V rows, dim = d taken from the variable count)."""
     scaled, rel, cancel = errors(R_gpu, R_ref, scale)
     tol = TOL[precision]
     assert np.all(np.isfinite(R_gpu)), f"{label}: non-finite output"
     assert np.all(scaled <= tol), f"{label}: scaled error {scaled.max():.3e} > {tol} ({scaled})"
-    if plain and precision == 64:
-        sel = cancel > 1e-3   # variables whose result does not cancel
-        assert np.all(rel[sel] <= PLAIN_TOL_F64), f"{label}: relative error {rel[sel].max():.3e}"
+    if plain:
+        sel = cancel > CANCEL_MIN   # variables whose result does not cancel
+        if precision == 32:
+            d = dim if dim is not None else {7: 2, 13: 3}[R_gpu.shape[0]]
+            sel[1 + d:] = False
+        assert np.all(rel[sel] <= PLAIN_TOL[precision]), (
+            f"{label}: plain relative error {rel[sel].max():.3e} > {PLAIN_TOL[precision]} "
+            f"(rows {np.nonzero(sel)[0]}, rel {rel}, |R|/|B| {cancel})")
     return scaled, rel
 
 

@@ -81,8 +81,8 @@ def test_tensor_core_gemm_pipelined_path(abi, K, lda):
     assert err < 3e-5 * max(1.0, np.sqrt(K / 100.0)), err
 
 
-def _history_case(abi, precision=64, n=(5, 4), order=1, steps=4):
-    """A small 2-D run with four history levels; returns host copies."""
+def _history_case(abi, precision=64, n=(5, 4), order=1, steps=4, dtau=1e-2):
+    """A small run with four history levels; returns host copies."""
     d = len(n)
     nv = 1 + d + d * d
     U0, mesh, prm, lo, hi = parity.make_case(n, order)
@@ -92,7 +92,7 @@ def _history_case(abi, precision=64, n=(5, 4), order=1, steps=4):
     abi.fr_dual_init(ctx, Ud)
     levels = [abi.unpack_state(ctx, Ud, nv)]
     for _ in range(steps):
-        abi.fr_dual_step(ctx, Ud, 1e-2, 1e-2, 1e-8, 400, check_every=10, allow_noconv=True)
+        abi.fr_dual_step(ctx, Ud, 1e-2, dtau, 1e-8, 400, check_every=10, allow_noconv=True)
         levels.append(abi.unpack_state(ctx, Ud, nv))
     return ctx, Ud, levels, nv
 
@@ -108,14 +108,24 @@ def _unflatten(flat, sizes):
     return out
 
 
-def test_loss_gradients_adam_and_prediction_match_oracle(abi):
-    ctx, Ud, levels, nv = _history_case(abi)
-    H = 32
-    net = abi.fr_mlp_create(ctx, H, 64, seed=7)
+MLP_CASES = [
+    # (mesh, order, hidden, samples): a small 2-D net, and the production
+    # shape of the dual-time workload's network (3-D p = 4: 4875 -> 256 ->
+    # 256 -> 1625) on 512 samples
+    ((5, 4), 1, 32, 40),
+    ((8, 8, 8), 4, 256, 512),
+]
+
+
+@pytest.mark.parametrize("n,order,H,S", MLP_CASES)
+def test_loss_gradients_adam_and_prediction_match_oracle(abi, n, order, H, S):
+    d = len(n)
+    ctx, Ud, levels, nv = _history_case(abi, n=n, order=order, dtau=1e-2 if d == 2 else 2e-3)
+    net = abi.fr_mlp_create(ctx, H, S, seed=7)
     try:
         K, Hh, NO, _, npar = abi.fr_mlp_info(net)
-        assert (K, Hh) == (3 * NO, H)
-        el = abi.fr_mlp_collect(net, 40, seed=3)
+        assert (K, Hh, NO) == (3 * NO, H, nv * (order + 1) ** d)
+        el = abi.fr_mlp_collect(net, S, seed=3)
         scales = abi.fr_mlp_params(net, 2, count=4 * nv)
         s0, s1, s2 = scales[:nv], scales[nv:2 * nv], scales[2 * nv:3 * nv]
         # the feature scales are the RMS of the blocks over the mesh
@@ -125,11 +135,11 @@ def test_loss_gradients_adam_and_prediction_match_oracle(abi):
         np.testing.assert_allclose(
             s2, np.sqrt(np.mean((Un - 2 * Unm1 + Unm2) ** 2, axis=(1, 2))), rtol=1e-5)
         # the collected samples are the oracle's features (to BF16) and raw targets
-        Xg = abi.fr_mlp_params(net, 3, count=K * 40).reshape(K, 40)
+        Xg = abi.fr_mlp_params(net, 3, count=K * S).reshape(K, S)
         Xo = omlp.features(Un, Unm1, Unm2, (s0, s1, s2), el)
         np.testing.assert_allclose(Xg, Xo, rtol=2 ** -8, atol=1e-30)
-        Tr = abi.fr_mlp_params(net, 4, count=NO * 40).reshape(NO, 40)
-        raw_o = (Unp1 - omlp.extrapolate(Un, Unm1, Unm2))[:, :, el].reshape(NO, 40)
+        Tr = abi.fr_mlp_params(net, 4, count=NO * S).reshape(NO, S)
+        raw_o = (Unp1 - omlp.extrapolate(Un, Unm1, Unm2))[:, :, el].reshape(NO, S)
         np.testing.assert_allclose(Tr, raw_o, rtol=1e-6, atol=1e-12 * np.abs(raw_o).max())
         loss = abi.fr_mlp_loss_grad(net)
         scales = abi.fr_mlp_params(net, 2, count=4 * nv)
@@ -176,7 +186,7 @@ def test_loss_gradients_adam_and_prediction_match_oracle(abi):
                 np.testing.assert_allclose(p0 - p1, p0 - pe, rtol=1e-4, atol=1e-7)
         # prediction from the three newest levels against the oracle network
         Ug = abi.new_state(ctx, 64)
-        Vg = abi.new_velocity(ctx, 2, 1)
+        Vg = abi.new_velocity(ctx, d, order)
         abi.fr_mlp_predict(net, Ug, Vg)
         torch.cuda.synchronize()
         G = abi.unpack_state(ctx, Ug, nv)
@@ -192,8 +202,8 @@ def test_loss_gradients_adam_and_prediction_match_oracle(abi):
         mag = mag.reshape(corr_ref.shape) * t[:, None, None]
         assert np.linalg.norm(corr_gpu - corr_ref) < BF16_TOL * np.linalg.norm(mag)
         stride, _, _ = abi.fr_layout(ctx)
-        V = Vg[:, :ne].cpu().numpy().reshape(2, -1, ne)
-        np.testing.assert_allclose(V, G[1:3], rtol=0, atol=1e-12)
+        V = Vg[:, :ne].cpu().numpy().reshape(d, -1, ne)
+        np.testing.assert_allclose(V, G[1:1 + d], rtol=0, atol=1e-12)
     finally:
         abi.fr_mlp_destroy(net)
         abi.fr_destroy(ctx)
@@ -346,3 +356,53 @@ def test_learned_guess_gain_in_3d_through_a_fork(abi):
         abi.fr_mlp_destroy(net)
         abi.fr_destroy(A)
         abi.fr_destroy(B)
+
+
+def test_save_load_round_trip(abi, tmp_path):
+    """A saved and reloaded network predicts bit for bit what the original
+    predicts, and training resumes from the saved Adam state: one more step
+    on the same samples gives identical weights.  Foreign and corrupt files
+    are refused."""
+    ctx, Ud, levels, nv = _history_case(abi)
+    net = abi.fr_mlp_create(ctx, 32, 64, seed=7)
+    net2 = None
+    other = abi.fr_create((5, 4), (0, 0), (1, 1), 2, nv, 2.5, 1e-3, 5e-3, 64)
+    path = str(tmp_path / "net.bin")
+    try:
+        abi.fr_mlp_collect(net, 40, seed=3)
+        abi.fr_mlp_train(net, 5, 1e-3)
+        U1, V1 = abi.new_state(ctx, 64), abi.new_velocity(ctx, 2, 1)
+        abi.fr_mlp_predict(net, U1, V1)
+        abi.fr_mlp_save(net, path)
+        net2 = abi.fr_mlp_load(ctx, path, capacity=64)
+        U2, V2 = abi.new_state(ctx, 64), abi.new_velocity(ctx, 2, 1)
+        abi.fr_mlp_predict(net2, U2, V2)
+        torch.cuda.synchronize()
+        assert torch.equal(U1, U2) and torch.equal(V1, V2)
+        _, _, _, _, npar = abi.fr_mlp_info(net)
+        assert np.array_equal(abi.fr_mlp_params(net, 0, count=npar),
+                              abi.fr_mlp_params(net2, 0, count=npar))
+        abi.fr_mlp_collect(net2, 40, seed=3)       # the same samples, same scales
+        l1 = abi.fr_mlp_train_step(net, 1e-3)
+        l2 = abi.fr_mlp_train_step(net2, 1e-3)
+        assert l1 == l2
+        assert np.array_equal(abi.fr_mlp_params(net, 0, count=npar),
+                              abi.fr_mlp_params(net2, 0, count=npar))
+        with pytest.raises(abi.FrError) as ei:       # another order
+            abi.fr_mlp_load(other, path)
+        assert ei.value.status == abi.FR_EINVAL
+        raw = bytearray(open(path, "rb").read())
+        raw[100] ^= 0x5A
+        bad = str(tmp_path / "bad.bin")
+        open(bad, "wb").write(bytes(raw))
+        with pytest.raises(abi.FrError) as ei:       # checksum
+            abi.fr_mlp_load(ctx, bad)
+        assert "checksum" in abi.fr_last_error()
+        with pytest.raises(abi.FrError):
+            abi.fr_mlp_load(ctx, str(tmp_path / "missing.bin"))
+    finally:
+        abi.fr_mlp_destroy(net)
+        if net2:
+            abi.fr_mlp_destroy(net2)
+        abi.fr_destroy(other)
+        abi.fr_destroy(ctx)

@@ -99,16 +99,20 @@ def test_conservation_on_gpu(abi, precision):
     assert np.all(np.abs(tot) < eps * mag), tot / mag
 
 
-@pytest.mark.parametrize("precision", [32, 64])
-def test_full_size_hex_p3_64cube_sampled(abi, precision):
+@pytest.mark.parametrize("precision,noise", [(32, False), (64, False), (32, True), (64, True)])
+def test_full_size_hex_p3_64cube_sampled(abi, precision, noise):
     """The 64^3, p = 3, 13-variable Taylor-Green workload in the launch
     configuration the benchmark times; 256 sampled elements (including the
-    mesh corners and the last CTA) against the oracle's per-element path."""
+    mesh corners and the last CTA) against the oracle's per-element path.
+    With the seeded U(-1e-3, 1e-3) noise the result no longer cancels in the
+    P and V rows, and the plain relative bound applies there too."""
     from paper_2107_14027_gb300 import workloads as W
     cfg = W.WORKLOADS["hex_p3_64cube"]
     n, order = cfg["n"], cfg["order"]
-    U = W.taylor_green(n, cfg["lo"], cfg["hi"], order,
-                       dtype=np.float32 if precision == 32 else np.float64)
+    U = W.taylor_green(n, cfg["lo"], cfg["hi"], order)
+    if noise:
+        U = W.add_noise(U)
+    U = U.astype(np.float32 if precision == 32 else np.float64)
     prm = fr.Params(cfg["zeta"], cfg["nu"], cfg["t_r"])
     mesh = fr.Mesh(n, cfg["lo"], cfg["hi"])
     ctx = abi.fr_create(n, cfg["lo"], cfg["hi"], order, 13, prm.zeta, prm.nu, prm.T, precision, 0)
@@ -131,7 +135,8 @@ def test_full_size_hex_p3_64cube_sampled(abi, precision):
     # term scale on the sampled elements: evaluate on a small mesh-independent
     # proxy by restricting the grid computation to the samples
     scale = _sampled_term_scale(U64, mesh, order, prm, elems)
-    parity.assert_parity(R[:, :, elems], R_ref, scale, precision, plain=False, label="64^3")
+    parity.assert_parity(R[:, :, elems], R_ref, scale, precision, plain=noise,
+                         label=f"64^3 noise={noise}")
 
 
 FULL_SIZE = [(1, 168, 32), (2, 112, 32), (3, 84, 32), (4, 67, 32), (5, 56, 32), (6, 48, 32),
