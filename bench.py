@@ -165,16 +165,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _cpu_baseline_subprocess(n_side, reps_s):
-    """Time the FP64 oracle RHS in a fresh single-threaded process on an
-    n_side^3 p = 3 sample of the workload; returns (gdof_per_s, seconds, desc)."""
-    code = f"""
-import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
-import numpy as np
+_ORACLE_PIECE = """
+import sys, time
+sys.path.insert(0, {root!r})
 from oracle import fr
 from paper_2107_14027_gb300 import workloads as W
-cfg = W.WORKLOADS[{WORKLOAD!r}]
+cfg = W.WORKLOADS[{workload!r}]
 n = ({n_side},) * 3
 h = (cfg['hi'][0] - cfg['lo'][0]) / cfg['n'][0]
 lo = (cfg['lo'][0],) * 3
@@ -182,24 +178,114 @@ hi = (cfg['lo'][0] + h * {n_side},) * 3
 U = W.taylor_green(n, lo, hi, cfg['order'])
 mesh = fr.Mesh(n, lo, hi)
 prm = fr.Params(cfg['zeta'], cfg['nu'], cfg['t_r'])
-fr.rhs(U, mesh, cfg['order'], prm)
-t0 = time.perf_counter(); k = 0
-while True:
-    fr.rhs(U, mesh, cfg['order'], prm); k += 1
-    if time.perf_counter() - t0 > {reps_s}:
-        break
-dt = (time.perf_counter() - t0) / k
-print(json.dumps({{"t": dt, "reps": k, "dof": U.size}}))
+def one():
+    fr.rhs(U, mesh, cfg['order'], prm)
 """
+
+_ORACLE_WORKER = _ORACLE_PIECE + """
+def work(seconds):
+    one()
+    t0 = time.perf_counter(); k = 0
+    while time.perf_counter() - t0 < seconds:
+        one(); k += 1
+    return k, time.perf_counter() - t0
+"""
+
+
+def _cpu_env():
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=600)
+    return env
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _cpu_baseline_runs(n_side, seconds):
+    """The FP64 oracle RHS on an n_side^3 p = 3 piece of the workload, timed
+    (a) in one single-threaded process and (b) in one single-threaded process
+    per host core at once (a spawned pool, started from a fresh interpreter,
+    so no GPU state is inherited).  Returns a dict of both rates (GDOF/s)."""
+    code = _ORACLE_WORKER.format(root=ROOT, workload=WORKLOAD, n_side=n_side) + f"""
+import json, multiprocessing as mp, os
+if __name__ == "__main__":
+    dof = U.size
+    k, t = work({seconds})
+    single = dof * k / t / 1e9
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(work, [{seconds}] * cores)
+        wall = time.perf_counter() - t0
+    allc = dof * sum(r[0] for r in res) / wall / 1e9
+    print(json.dumps({{"single": single, "single_reps": k, "single_s": t / k, "all": allc,
+                      "cores": cores, "all_reps": sum(r[0] for r in res), "wall": wall}}))
+"""
+    path = os.path.join("/tmp", f"acmhd_oracle_baseline_{os.getpid()}.py")
+    with open(path, "w") as f:
+        f.write(code)
+    try:
+        r = subprocess.run([sys.executable, path], capture_output=True, text=True, env=_cpu_env(),
+                           timeout=900)
+    finally:
+        os.unlink(path)
     if r.returncode != 0:
         return None
-    res = json.loads(r.stdout.strip().splitlines()[-1])
-    return res["dof"] / res["t"] / 1e9, res["t"], res["reps"]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _err_vs_oracle(U, R, mesh_n, cfg, elems):
+    """Per-variable error of the timed output R (sampled columns `elems`)
+    against the oracle's per-element path on the same FP32-rounded input
+    (part of the CPU-baseline leg): RMS error over RMS of the oracle's
+    result (plain) and over RMS of the summed terms (scaled)."""
+    from oracle import acmhd, fr
+    from oracle.ops1d import Ops1D
+    order = cfg["order"]
+    mesh = fr.Mesh(mesh_n, cfg["lo"], cfg["hi"])
+    prm = fr.Params(cfg["zeta"], cfg["nu"], cfg["t_r"])
+    U64 = U.astype(np.float64)
+    t0 = time.perf_counter()
+    R_ref = fr.rhs_dense(U64, mesh, order, prm, elems=elems)
+    t_ref = time.perf_counter() - t0
+    ops = Ops1D(order)
+    m = ops.m
+    Dt = ops.D - np.outer(ops.dhl, ops.lm) - np.outer(ops.dhr, ops.lp)
+    Ue = U64[:, :, elems].reshape(U.shape[0], m, m, m, len(elems))
+    B = np.abs(acmhd.source(Ue, prm.T))
+    for a in range(3):
+        F = np.abs(acmhd.flux(Ue, a, prm.zeta, prm.nu, prm.T))
+        ax = 3 - a
+        B = B + (2.0 / mesh.h[a]) * np.moveaxis(np.tensordot(np.abs(Dt), F, axes=([1], [ax])),
+                                                0, ax)
+    B = B.reshape(U.shape[0], m ** 3, len(elems))
+    diff = np.sqrt(np.mean((R - R_ref) ** 2, axis=(1, 2)))
+    ref = np.sqrt(np.mean(R_ref ** 2, axis=(1, 2)))
+    scale = np.sqrt(np.mean(B ** 2, axis=(1, 2)))
+    names = ["P", "u", "v", "w"] + [f"{g}{x}" for g in "qrs" for x in "xyz"]
+    return {"elements": int(len(elems)), "oracle": "FP64 per-element (dense) path",
+            "plain": {k: float(v) for k, v in zip(names, diff / np.maximum(ref, 1e-300))},
+            "scaled": {k: float(v) for k, v in zip(names, diff / np.maximum(scale, 1e-300))},
+            "max_scaled": float(np.max(diff / np.maximum(scale, 1e-300))),
+            "oracle_s": t_ref}
 
 
 def run_reference(args):
@@ -273,10 +359,10 @@ def run_gpu(args):
     m = order + 1
     dof = int(np.prod(n)) * m ** 3 * nv
 
-    # CPU baseline first (fresh single-threaded process; no GPU state inherited)
+    # CPU baseline first (fresh processes; no GPU state inherited)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline_subprocess(16, 10.0)
+        cpu = _cpu_baseline_runs(16, 10.0)
 
     stream = torch.cuda.current_stream()
     U32 = W.taylor_green(n, cfg["lo"], cfg["hi"], order, dtype=np.float32)
@@ -312,6 +398,17 @@ def run_gpu(args):
     t_max = _max_over_ranks(dist, t_total, "cuda")
     value = _job_rate(dof * args.steps, world, t_max) / 1e9
 
+    # error of the timed output against the oracle on sampled elements
+    # (mesh corners, the last tile, 250 seeded others): CPU-baseline leg
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(0)
+        elems = np.unique(np.concatenate([[0, n[0] - 1, ne - n[0], ne - 1, (ne - 1) // 32 * 32],
+                                          rng.choice(ne, 250, replace=False)]))
+        idx = torch.as_tensor(elems, device="cuda")
+        Rs = Rd[:, :ne].index_select(1, idx).cpu().numpy().astype(np.float64)
+        err = _err_vs_oracle(U32, Rs.reshape(nv, m ** 3, len(elems)), n, cfg, elems)
+
     # per-kernel timing on the launching stream: the trace kernel alone
     # (fr_trace) and the fused kernel alone (fr_rhs_volume, reading the
     # traces of the same U)
@@ -320,22 +417,31 @@ def run_gpu(args):
     trace_s = _time_loop(lambda: abi.fr_trace(ctx, Ud, stream), stream, K, 2, torch) / K
     fused_s = _time_loop(lambda: abi.fr_rhs_volume(ctx, Ud, Rd, stream), stream, K, 2, torch) / K
 
-    # algorithmic bytes of one fused launch (FP32).  Byte model of the method
-    # (per element, n_v (2 m^3 + 6 m^2) values: read U and the traces of all
-    # variables on the six faces, write R) and this kernel's own minimum (read
-    # U, write R, read the 7 normal-flux slots on the four y/z faces; x faces
-    # come from neighbouring lanes except at the ends of each 32-element group)
-    alg_bytes = ne * nv * (2 * m ** 3 + 6 * m ** 2) * 4
-    own_bytes = ne * (2 * nv * m ** 3 + 4 * 7 * m ** 2) * 4 + (ne // 32) * 2 * 7 * m ** 2 * 4
+    # algorithmic bytes of one fused launch (FP32), the method's own: read U
+    # (n_v m^3 per element), write R (n_v m^3), and read the neighbours' face
+    # traces of the 1 + 2d variables the normal flux needs on each of the 2d
+    # faces (the paper's sparsity of the ACM-HD flux, Sec. 3).  The dense
+    # model (all n_v variables on all faces, n_v (2 m^3 + 6 m^2)) is kept as
+    # a second figure.
+    d = 3
+    alg_bytes = ne * (2 * nv * m ** 3 + 2 * d * (1 + 2 * d) * m ** 2) * 4
+    dense_bytes = ne * nv * (2 * m ** 3 + 6 * m ** 2) * 4
     hbm, peak_kind = _peaks()
     achieved = alg_bytes / fused_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": _profiled_traffic(),
                 "kernel": "fused_kernel<3,4,float>", "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes,
-                "own_min_bytes_per_launch": own_bytes,
-                "achieved_own": own_bytes / fused_s / 1e9,
-                "frac_own": own_bytes / fused_s / 1e9 / hbm}
+                "byte_model": "per element 4 (2 n_v m^3 + 2d (1+2d) m^2)",
+                "dense_model": {"bytes_per_launch": dense_bytes,
+                                "achieved": dense_bytes / fused_s / 1e9,
+                                "frac": dense_bytes / fused_s / 1e9 / hbm,
+                                "model": "per element 4 n_v (2 m^3 + 6 m^2)"}}
+    # the whole RHS (trace + fused) on the same sparse model: U read twice,
+    # R written, traces written and read once
+    rhs_bytes = ne * (3 * nv * m ** 3 + 2 * 2 * d * (1 + 2 * d) * m ** 2) * 4
+    rhs_roofline = {"bytes_per_rhs": rhs_bytes, "achieved": rhs_bytes / t_rhs_only / 1e9,
+                    "frac": rhs_bytes / t_rhs_only / 1e9 / hbm}
 
     # unfused pipeline and FP64 fused, same stream
     t_unf = _time_loop(lambda: abi.fr_rhs_unfused(ctx, Ud, Rd, stream), stream, K, 2, torch) / K
@@ -350,9 +456,23 @@ def run_gpu(args):
     Rd64 = abi.new_state(ctx64, abi.FR_F64)
     t64 = _time_loop(lambda: abi.fr_rhs(ctx64, Ud64, Rd64, stream), stream, max(K // 2, 5), 2,
                      torch) / max(K // 2, 5)
+    t64_fused = _time_loop(lambda: abi.fr_rhs_volume(ctx64, Ud64, Rd64, stream), stream,
+                           max(K // 2, 5), 2, torch) / max(K // 2, 5)
     abi.fr_destroy(ctx64)
     del Ud64, Rd64
     torch.cuda.empty_cache()
+    # FMA peaks of this GPU (probe kernel), FP64 and FP32
+    probe = {p: _fma_peak(abi, p, stream, torch) for p in (abi.FR_F64, abi.FR_F32)}
+    # FP64 is arithmetic-bound on GB300: the fused kernel's algorithmic flops
+    # (per point 42 m + 195: 21 flux components contracted along their axis,
+    # 2 m flops each; corrections; flux and source) against the FP64 peak
+    flops64 = ne * m ** 3 * (42 * m + 195)
+    fp64_roofline = {"bound": "alu", "achieved": flops64 / t64_fused / 1e12,
+                     "peak": probe[abi.FR_F64] / 1e12, "unit": "TFLOP/s",
+                     "frac": flops64 / t64_fused / probe[abi.FR_F64],
+                     "kernel": "fused_kernel<3,4,double>", "flops_per_launch": flops64,
+                     "flop_model": "per point 42 m + 195",
+                     "peak_source": "measured by the FMA probe kernel (fr_fma_probe)"}
 
     # end to end through the public host-buffer call
     ctx = abi.fr_create(n, cfg["lo"], cfg["hi"], order, nv, cfg["zeta"], cfg["nu"], cfg["t_r"],
@@ -388,21 +508,49 @@ def run_gpu(args):
                        "parallelism": f"replicas{world}"},
             "e2e": e2e,
             "roofline": roofline,
+            "rhs_roofline": rhs_roofline,
             "kernels_ms": {"fused": 1e3 * fused_s, "trace": 1e3 * trace_s,
                            "rhs": 1e3 * t_rhs_only},
             "unfused": {"value": dof / t_unf / 1e9, "ms": 1e3 * t_unf,
                         "fused_speedup": t_unf / t_rhs_only},
-            "fp64": {"value": dof / t64 / 1e9, "ms": 1e3 * t64},
+            "fp64": {"value": dof / t64 / 1e9, "ms": 1e3 * t64, "fused_ms": 1e3 * t64_fused,
+                     "roofline": fp64_roofline},
+            "fma_peak_tflops": {"fp64": probe[abi.FR_F64] / 1e12,
+                                "fp32": probe[abi.FR_F32] / 1e12},
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
         }
+        if err is not None:
+            out["err_vs_oracle"] = err
         if cpu is not None:
-            out["cpu_baseline"] = {"value": cpu[0], "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-                                   "sample": f"FP64 oracle RHS, 16^3-element p=3 piece of the "
-                                             f"workload, {cpu[2]} reps, {cpu[1]:.2f} s each"}
+            out["cpu_baseline"] = {
+                "value": cpu["all"], "unit": "GDOF/s", "cores": cpu["cores"], "kind": "oracle",
+                "cpu_model": _cpu_model(), "nproc": os.cpu_count(),
+                "single_core": {"value": cpu["single"], "cores": 1, "reps": cpu["single_reps"],
+                                "s_per_rhs": cpu["single_s"]},
+                "sample": (f"FP64 numpy oracle RHS (sum-factorised) on a 16^3-element p=3 piece "
+                           f"of the workload: one process per core ({cpu['cores']}), "
+                           f"{cpu['all_reps']} RHS in {cpu['wall']:.1f} s; single core "
+                           f"{cpu['single_reps']} RHS, {cpu['single_s']:.2f} s each")}
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _fma_peak(abi, precision, stream, torch):
+    """FLOP/s of the FMA probe kernel, iterations sized to about 20 ms."""
+    out = torch.zeros(152 * 8 * 8 * 4, dtype=torch.float64, device="cuda")
+    iters = 64
+    for _ in range(4):
+        flops = abi.fr_fma_probe(precision, iters, out, stream)
+        t = _time_loop(lambda: abi.fr_fma_probe(precision, iters, out, stream), stream, 3, 1,
+                       torch) / 3
+        if t > 0.01:
+            break
+        iters = int(iters * min(64.0, 0.02 / max(t, 1e-6)))
+    t = _time_loop(lambda: abi.fr_fma_probe(precision, iters, out, stream), stream, 10, 2,
+                   torch) / 10
+    return flops / t
 
 
 def run_dual(args):

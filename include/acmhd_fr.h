@@ -362,6 +362,16 @@ int fr_mlp_load(fr_ctx* ctx, const char* path, int capacity, fr_mlp** out);
 int fr_gemm_bf16(int amode, int bmode, int N, int M, int K, const void* A, long long lda,
                  const void* B, long long ldb, float* C, long long ldc, void* stream);
 
+/* Arithmetic peak probe (a measuring utility; no counterpart in the
+ * paper): launches one kernel that does only fused multiply-adds in FP32 or
+ * FP64 (precision FR_F32 / FR_F64), `iters` x 128 per thread on every SM,
+ * and stores *flops, the floating-point operations it performs (2 per FMA).
+ * The caller times it (CUDA events on `stream`) to obtain this GPU's FMA
+ * throughput, the roofline denominator of an arithmetic-bound kernel.
+ * `out` is a device buffer of at least 8 * (SM count) * 8 bytes that the
+ * kernel may write (it never does for valid inputs).  Asynchronous. */
+int fr_fma_probe(int precision, int iters, void* out, double* flops, void* stream);
+
 /* Synchronises `stream` and reports an asynchronous CUDA error (a failed
  * kernel) as FR_ECUDA with its text in fr_last_error(); FR_OK otherwise. */
 int fr_check(fr_ctx* ctx, void* stream);

@@ -27,7 +27,7 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", 
            "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity", "fr_dual_copy",
            "fr_mlp_create", "fr_mlp_destroy", "fr_mlp_info", "fr_mlp_collect", "fr_mlp_loss_grad",
            "fr_mlp_train", "fr_mlp_predict", "fr_mlp_predict_for", "fr_mlp_params", "fr_gemm_bf16",
-           "fr_mlp_train_step", "fr_mlp_save", "fr_mlp_load"]
+           "fr_mlp_train_step", "fr_mlp_save", "fr_mlp_load", "fr_fma_probe"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -99,6 +99,7 @@ def _lib():
         lib.fr_mlp_predict_for.argtypes = [vp, vp, vp, vp, vp]
         lib.fr_mlp_params.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float), sz, i32]
         lib.fr_mlp_train_step.argtypes = [vp, dbl, dp, vp]
+        lib.fr_fma_probe.argtypes = [i32, i32, vp, dp, vp]
         lib.fr_mlp_save.argtypes = [vp, ctypes.c_char_p]
         lib.fr_mlp_load.argtypes = [vp, ctypes.c_char_p, i32, ctypes.POINTER(vp)]
         lib.fr_gemm_bf16.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.c_longlong, vp,
@@ -370,6 +371,14 @@ def fr_gemm_bf16(amode, bmode, N, M, K, A, lda, B, ldb, C, ldc, stream=None):
     _check(_lib().fr_gemm_bf16(int(amode), int(bmode), int(N), int(M), int(K), _ptr(A), int(lda),
                                _ptr(B), int(ldb), _ptr(C), int(ldc), _stream(stream)),
            "fr_gemm_bf16")
+
+
+def fr_fma_probe(precision, iters, out, stream=None):
+    """Launches the FMA peak probe; returns the FLOPs the launch performs."""
+    flops = ctypes.c_double()
+    _check(_lib().fr_fma_probe(int(precision), int(iters), _ptr(out), ctypes.byref(flops),
+                               _stream(stream)), "fr_fma_probe")
+    return flops.value
 
 
 def fr_check(ctx, stream=None):

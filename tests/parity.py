@@ -12,11 +12,22 @@ to the result, so the parity bound for variable v is
 with tol = 1e-12 (FP64) and 2e-5 (FP32), the oracle evaluated in FP64 on
 the identical (already rounded) input values.  Where the result does not
 cancel, the plain relative bound || dR_v || <= tol || R_oracle,v || must
-hold as well: in FP64 for every variable whose || R_v || / || B_v || exceeds
-1e-3, and in FP32 for the P and V rows under the same condition (the
-auxiliary rows' result (grad u - q)/T cancels by up to 1e5 against its
-terms, so their plain FP32 error is reported, not bounded).
+hold as well, for every variable whose || R_v || / || B_v || is at least
+CANCEL_MIN[precision].  That threshold follows from the arithmetic: any
+evaluation in a precision with unit roundoff u carries an error of about
+k u || B_v || (k a small count of roundings; measured k ~ 1-2 here), so the
+plain bound tol || R_v || is attainable only where || R_v || / || B_v || >=
+k u / tol.  With k = 8: FP32 (u = 2^-24) 2.4e-2, FP64 (u = 2^-53) 1e-3
+(k u / tol ~ 1e-3 too).  Rows whose result cancels further (the auxiliary
+rows' (grad u - q)/T by up to 1e5; P and V of nearly divergence-free or
+steady fields) are held to the scaled bound.
+
+With ACMHD_PARITY_LOG=<path> set, every check appends one JSON line (label,
+precision, per-variable scaled and plain errors, |R|/|B|) to that file.
 """
+import json
+import os
+
 import numpy as np
 
 from oracle import acmhd, fr
@@ -25,7 +36,7 @@ from paper_2107_14027_gb300 import workloads as W
 
 TOL = {32: 2e-5, 64: 1e-12}
 PLAIN_TOL = {32: 2e-5, 64: 1e-12}
-CANCEL_MIN = 1e-3
+CANCEL_MIN = {32: 8 * 2.0 ** -24 / 2e-5, 64: 1e-3}
 
 
 def term_scale(U, mesh, order, prm, corr="dg"):
@@ -54,19 +65,22 @@ def errors(R_gpu, R_ref, scale):
     return scaled, diff / np.maximum(ref, 1e-300), ref / safe
 
 
-def assert_parity(R_gpu, R_ref, scale, precision, plain=False, label="", dim=None):
+def assert_parity(R_gpu, R_ref, scale, precision, plain=False, label=""):
     """Scaled bound on every variable; with `plain`, the plain relative bound
-    on the variables whose result does not cancel (FP64: all rows; FP32: the
-    P and V rows, dim = d taken from the variable count)."""
+    on the variables whose result does not cancel (|R|/|B| >= CANCEL_MIN)."""
     scaled, rel, cancel = errors(R_gpu, R_ref, scale)
     tol = TOL[precision]
+    log = os.environ.get("ACMHD_PARITY_LOG")
+    if log:
+        with open(log, "a") as f:
+            f.write(json.dumps({"label": label, "precision": precision,
+                                "scaled": [float(x) for x in scaled],
+                                "plain": [float(x) for x in rel],
+                                "cancel": [float(x) for x in cancel]}) + "\n")
     assert np.all(np.isfinite(R_gpu)), f"{label}: non-finite output"
     assert np.all(scaled <= tol), f"{label}: scaled error {scaled.max():.3e} > {tol} ({scaled})"
     if plain:
-        sel = cancel > CANCEL_MIN   # variables whose result does not cancel
-        if precision == 32:
-            d = dim if dim is not None else {7: 2, 13: 3}[R_gpu.shape[0]]
-            sel[1 + d:] = False
+        sel = cancel >= CANCEL_MIN[precision]   # variables whose result does not cancel
         assert np.all(rel[sel] <= PLAIN_TOL[precision]), (
             f"{label}: plain relative error {rel[sel].max():.3e} > {PLAIN_TOL[precision]} "
             f"(rows {np.nonzero(sel)[0]}, rel {rel}, |R|/|B| {cancel})")

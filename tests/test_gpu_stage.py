@@ -150,8 +150,8 @@ def test_fused_stage_full_size_step_matches_separate_update(abi):
 
 @pytest.mark.parametrize("n,order,precision", [((32, 2, 8), 3, 32), ((32, 5), 2, 64)])
 def test_pseudo_solve_on_every_schedule_gives_the_same_state(abi, n, order, precision):
-    """Layer sweep + separate update, two kernels + separate update and the
-    fused stage: one state, bit for bit, after fixed iterations."""
+    """Two kernels + separate update, the fused stage and the automatic
+    choice: one state, bit for bit, after fixed iterations."""
     d = len(n)
     ctx, U, nv = _ctx(abi, n, order, precision)
     rng = np.random.default_rng(5)
@@ -159,8 +159,8 @@ def test_pseudo_solve_on_every_schedule_gives_the_same_state(abi, n, order, prec
     try:
         stride, ne, _ = abi.fr_layout(ctx)
         out = []
-        for sched in (abi.FR_SCHEDULE_SWEEP, abi.FR_SCHEDULE_TWO_KERNELS,
-                      abi.FR_SCHEDULE_FUSED_STAGE):
+        for sched in (abi.FR_SCHEDULE_TWO_KERNELS, abi.FR_SCHEDULE_FUSED_STAGE,
+                      abi.FR_SCHEDULE_AUTO):
             abi.fr_set_schedule(ctx, sched)
             Ud = abi.pack_state(ctx, U, precision)
             V = abi.new_velocity(ctx, d, order)
@@ -173,7 +173,7 @@ def test_pseudo_solve_on_every_schedule_gives_the_same_state(abi, n, order, prec
             assert st == abi.FR_ENOCONV and it == 6
             out.append((Ud, V))
         torch.cuda.synchronize()
-        abi.fr_check(ctx)                         # the sweep's bounded waits did not time out
+        abi.fr_check(ctx)                         # no asynchronous error
         for Ux, Vx in out[1:]:
             assert torch.equal(out[0][0][:, :ne], Ux[:, :ne])
             assert torch.equal(out[0][1][:, :ne], Vx[:, :ne])
