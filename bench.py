@@ -577,12 +577,30 @@ def run_dual(args):
     n_warm, n_collect, n_held = 3, args.dual_collect_steps, args.dual_held_steps
     per_step = max(1, args.dual_samples // n_collect)
     U0 = W.taylor_green(n, lo, hi, order, dtype=np.float32 if prec == abi.FR_F32 else np.float64)
-    solvers = []
+    solvers, pmgs = [], []
+    factors = None
+    if args.dual_pmg_factors:
+        fs = [float(x) for x in args.dual_pmg_factors.split(",")]
+        factors = {order - i: f for i, f in enumerate(fs)}
     for _ in range(2):
         c32 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, prec)
         c64 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, abi.FR_F64) if refine else None
         solvers.append([c32, c64, abi.pack_state(c32, U0, prec),
                         abi.new_state(c64, abi.FR_F64) if refine else None])
+        pm = [None, None]
+        if args.dual_pmg:
+            for j, c in enumerate((c32, c64)):
+                if c is None:
+                    continue
+                pm[j] = abi.fr_pmg_create(c, 1)
+                abi.fr_pmg_set_dtau(pm[j], factors, not args.dual_pmg_explicit)
+                if args.dual_anderson and (j == 1 or not refine or args.dual_anderson_fp32):
+                    abi.fr_pmg_set_anderson(pm[j], args.dual_anderson)
+                if args.dual_pmg_bottom or args.dual_pmg_top:
+                    sched = [(q, 1) for q in range(order, 1, -1)] + [(1, args.dual_pmg_bottom or 4)]
+                    sched += [(q, 1) for q in range(2, order)] + [(order, args.dual_pmg_top or 7)]
+                    abi.fr_pmg_set_cycle(pm[j], sched)
+        pmgs.append(pm)
     abi.fr_dual_init(solvers[0][0], solvers[0][2])
     net = abi.fr_mlp_create(solvers[0][0], args.dual_hidden, per_step * n_collect, seed=2021)
     log = {"A": [], "B": []}
@@ -591,10 +609,12 @@ def run_dual(args):
         c32, c64, U, U64 = solvers[which]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, s = abi.fr_dual_step(c32, U, dt, dtau, tol, max_iter, check_every=5, guess=guess,
+        pm = pmgs[which]
+        cap = max(1, max_iter // args.dual_pmg_iters_per_cycle) if args.dual_pmg else max_iter
+        st, s = abi.fr_dual_step(c32, U, dt, dtau, tol, cap, check_every=5, guess=guess,
                                  refine=c64 if refine else None,
                                  U_refine=U64 if refine else None, tol_switch=tol_switch,
-                                 mlp=net, allow_noconv=True)
+                                 mlp=net, allow_noconv=True, pmg=pm[0], refine_pmg=pm[1])
         torch.cuda.synchronize()
         rec = {"step": k, "wall_s": time.perf_counter() - t0, "iters_fp32": s.iters,
                "iters_fp64": s.iters_refine, "res": s.res, "res_switch": s.res_switch,
@@ -632,7 +652,11 @@ def run_dual(args):
         "dtype": "f64" if prec == abi.FR_F64 else "f32+f64", "data": "synthetic",
         "config": {"workload": f"hex_p{order}_{args.dual_mesh}cube_dual", "order": order,
                    "mesh": list(n), "dt": dt, "dtau": dtau, "tol": tol,
-                   "tol_switch": tol_switch, "bdf": 2, "pseudo": "RK4",
+                   "tol_switch": tol_switch, "bdf": 2,
+                   "pseudo": ("P-multigrid cycles (iters count cycles)" if args.dual_pmg
+                              else "RK4"),
+                   "pmg_factors": args.dual_pmg_factors, "pmg_implicit": not args.dual_pmg_explicit,
+                   "anderson": args.dual_anderson, "anderson_fp32": args.dual_anderson_fp32,
                    "max_iter_train_steps": args.dual_train_iters,
                    "max_iter_held_steps": args.dual_held_iters,
                    "mlp": {"hidden": args.dual_hidden, "samples": per_step * n_collect,
@@ -643,6 +667,10 @@ def run_dual(args):
         "steps": {"plain": log["A"], "learned": log["B"]},
     }
     print(json.dumps(out))
+    for pm in pmgs:
+        for x in pm:
+            if x is not None:
+                abi.fr_pmg_destroy(x)
     for c32, c64, _, _ in solvers:
         abi.fr_destroy(c32)
         if c64 is not None:
@@ -837,6 +865,23 @@ def main():
                     help="pseudo-iteration cap of the steps before the held-out ones")
     ap.add_argument("--dual-held-iters", type=int, default=600,
                     help="pseudo-iteration cap of the held-out steps")
+    ap.add_argument("--dual-pmg", action="store_true",
+                    help="P-multigrid cycles for the pseudo-iterations (orders p .. 1)")
+    ap.add_argument("--dual-pmg-factors", default="",
+                    help="pseudo-step multipliers for orders p, p-1, .., 1 (default 1.75^(p-q))")
+    ap.add_argument("--dual-pmg-explicit", action="store_true",
+                    help="no point-implicit scaling of the stiff linear terms")
+    ap.add_argument("--dual-pmg-bottom", type=int, default=0,
+                    help="iterations on the coarsest order per cycle (default 4)")
+    ap.add_argument("--dual-pmg-top", type=int, default=0,
+                    help="iterations on the finest order at the end of a cycle (default 7)")
+    ap.add_argument("--dual-anderson", type=int, default=0,
+                    help="Anderson mixing memory over the P-multigrid cycles (FP64 phase)")
+    ap.add_argument("--dual-anderson-fp32", action="store_true",
+                    help="also mix the cycles of the FP32 phase")
+    ap.add_argument("--dual-pmg-iters-per-cycle", type=int, default=10,
+                    help="fine-iteration equivalents of one cycle, to turn the iteration "
+                         "caps into cycle caps")
     ap.add_argument("--dual-tol", type=float, default=1e-6,
                     help="residual tolerance; below the FP32 floor (5e-6) an FP64 twin refines")
     args = ap.parse_args()

@@ -258,6 +258,63 @@ int fr_pseudo_solve(fr_ctx* ctx, void* U, double* V, const double* Vn, const dou
  * the widened state until tol; the result is narrowed back into U.  The
  * FP64 velocity master and the history stay in ctx.
  * fr_dual_velocity copies the newest FP64 velocity level into V (device). */
+/* P-multigrid pseudo solver (Sec. 5: the Taylor-Green runs accelerate their
+ * pseudo-iterations by P-multigrid over the orders of the same mesh, in an
+ * asymmetric cycle of (order, iterations) pairs - (4,1) (3,1) (2,1) (1,4)
+ * (2,1) (3,1) (4,7) at p = 4 - with the pseudo step enlarged by a constant
+ * factor, 1.75, per order below the finest).  Full approximation scheme
+ * with N(U) = R(U) - I_V (a0/dt) V: going down from order q to q - 1 the
+ * state and the residual N + g are restricted (per element and direction,
+ * L2 projection onto degree q - 1) and the coarse forcing is
+ * g = I_r (N_q(U) + g_q) - N_{q-1}(I_r U); going up the coarse correction
+ * U_{q-1} - I_r U_q is interpolated and added (to the FP64 velocity master
+ * on the finest level).  Each entry of the cycle moves one order (restrict
+ * or prolong) and then takes its iterations of classical RK4 in pseudo time
+ * on dU/dtau = D (N(U) + g), D = 1 on P, 1 / (1 + dtau a0/dt) on the
+ * velocity and 1 / (1 + dtau / T_r) on the gradient rows (point-implicit
+ * scaling of the two linear stiff terms; it does not change the converged
+ * state; fr_pmg_set_dtau can switch it off).
+ *   fr_pmg_create      levels of order coarsest_order .. p - 1 of ctx's
+ *                      discretization (internal contexts and four state
+ *                      buffers each, allocated here); default cycle: one
+ *                      iteration per order down, 4 on the coarsest, one
+ *                      per order up, 7 on the finest; pseudo step of order
+ *                      q: dtau 1.75^(p - q); scaling on.
+ *   fr_pmg_set_cycle   n entries (orders[i], iters[i]): starts and ends at
+ *                      p with iters[0] >= 1, consecutive orders differ by
+ *                      at most one, orders within coarsest .. p.
+ *   fr_pmg_set_dtau    factor[q] (q = coarsest .. p; array indexed by
+ *                      order) multiplies dtau on order q; NULL keeps the
+ *                      factors; implicit 0/1 switches the scaling.
+ *   fr_pmg_solve       the pseudo-iteration of fr_pseudo_solve with cycles
+ *                      instead of RK4 steps: the residual (RMS of R_tau over
+ *                      the velocity DOFs, FP64) of the state at the start of
+ *                      each cycle decides convergence (tol), max_cycles and
+ *                      stall as fr_pseudo_solve's max_iter and stall; one
+ *                      host synchronisation per cycle; *cycles and *res as
+ *                      there.  U, V, Vn, Vnm1, dt, bdf_order, dtau: as
+ *                      fr_pseudo_solve (dtau is the finest level's step).
+ * All levels run in the precision of ctx. */
+typedef struct fr_pmg fr_pmg;
+int fr_pmg_create(fr_ctx* ctx, int coarsest_order, fr_pmg** out);
+void fr_pmg_destroy(fr_pmg* pmg);
+int fr_pmg_set_cycle(fr_pmg* pmg, int n, const int* orders, const int* iters);
+int fr_pmg_set_dtau(fr_pmg* pmg, const double* factor, int implicit);
+/* Anderson mixing over the cycles of fr_pmg_solve (not in the paper; Walker
+ * & Ni 2011): after cycle k, with G(x_j) the state a cycle produced from
+ * x_j and f_j = G(x_j) - x_j over the last memory + 1 cycles of this solve,
+ * the next state is G(x_k) - dG gamma, gamma minimising || f_k - dF gamma ||
+ * (dF, dG: successive differences; inner products over the real elements,
+ * the velocity through its FP64 master; normal equations, regularised by
+ * 1e-13 of their largest diagonal entry, oldest columns dropped while they
+ * are singular).  memory 0 switches it off; memory < 16.  Allocates
+ * 2 (memory + 1) + 1 copies of the state and the velocity (freed by
+ * fr_pmg_destroy or the next call); one host synchronisation per cycle. */
+int fr_pmg_set_anderson(fr_pmg* pmg, int memory);
+int fr_pmg_solve(fr_pmg* pmg, void* U, double* V, const double* Vn, const double* Vnm1,
+                 double dt, int bdf_order, double dtau, double tol, int max_cycles,
+                 double stall, int* cycles, double* res, void* stream);
+
 typedef struct fr_dual_opts {
     double dt, dtau;      /* physical and pseudo time steps (> 0) */
     double tol;           /* residual tolerance (RMS of R_tau over velocity DOFs) */
@@ -270,11 +327,15 @@ typedef struct fr_dual_opts {
     fr_mlp* mlp;          /* trained network for FR_GUESS_MLP (created on this
                              context or one of the same discretization; the
                              guess comes from this context's history) */
+    fr_pmg* pmg;          /* NULL, or a P-multigrid solver created on ctx: the
+                             pseudo-iteration runs fr_pmg_solve, max_iter
+                             counting cycles */
+    fr_pmg* refine_pmg;   /* the same for the refinement context */
 } fr_dual_opts;
 
 typedef struct fr_dual_stats {
-    int iters;            /* pseudo iterations in ctx */
-    int iters_refine;     /* pseudo iterations in refine */
+    int iters;            /* pseudo iterations (cycles with P-multigrid) in ctx */
+    int iters_refine;     /* pseudo iterations (cycles) in refine */
     double res;           /* final residual */
     double res_switch;    /* residual when ctx handed over (or final) */
     int guess_used;       /* FR_GUESS_* actually used (the MLP guess falls back) */

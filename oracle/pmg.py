@@ -34,13 +34,18 @@ formulas; the readings taken here:
   * convergence: the finest level's velocity residual (RMS of N + g over
     the velocity rows), taken at the start of each cycle.
 
+Anderson mixing over the cycles (Anderson class; not in the paper) is an
+option of pseudo_solve.
+
 Pins (tests/test_oracle_pmg.py): transfer operators exact on polynomials
 (prolongation of degree <= q-1, restriction reproduces them, restriction
 after prolongation is the identity, the projection error is orthogonal to
 the coarse space); the scaled RK4 step on a pure relaxation equation is the
 RK4 stability polynomial of -lambda dtau / (1 + lambda dtau); a converged
 state is a fixed point of a cycle; cycles converge to the same state as
-plain RK4 pseudo-stepping.
+plain RK4 pseudo-stepping; Anderson mixing terminates on a linear map of
+dimension n within n + 1 steps (its equivalence with GMRES) and is the plain
+iteration for m = 0.
 """
 import numpy as np
 
@@ -159,18 +164,45 @@ def fine_residual(level, U, g, a0dt):
     return timestep.velocity_residual(level.N(U, a0dt) + g, d)
 
 
+class Anderson:
+    """Anderson mixing of a fixed-point iteration x <- G(x) with memory m
+    (Walker & Ni, SIAM J. Numer. Anal. 49, 2011, the undamped form; not in
+    the paper): with f_j = G(x_j) - x_j over the last m + 1 iterates,
+    gamma = argmin || f_k - dF gamma ||_2 (dF, dG the columns of successive
+    differences of f and G), x_{k+1} = G(x_k) - dG gamma; with one iterate
+    in the window, x_{k+1} = G(x_k).  m = 0 is the plain iteration."""
+
+    def __init__(self, m):
+        self.m, self.G, self.F = m, [], []
+
+    def step(self, x, gx):
+        if self.m == 0:
+            return gx
+        self.G.append(gx.copy())
+        self.F.append(gx - x)
+        self.G, self.F = self.G[-(self.m + 1):], self.F[-(self.m + 1):]
+        if len(self.F) == 1:
+            return gx
+        dF = np.stack([(self.F[i + 1] - self.F[i]).ravel() for i in range(len(self.F) - 1)], 1)
+        dG = np.stack([(self.G[i + 1] - self.G[i]).ravel() for i in range(len(self.G) - 1)], 1)
+        gamma = np.linalg.lstsq(dF, self.F[-1].ravel(), rcond=None)[0]
+        return (self.G[-1].ravel() - dG @ gamma).reshape(x.shape)
+
+
 def pseudo_solve(levels, U0, Un, Unm1, dt, bdf_order, dtau, tol, max_cycles, schedule,
-                 factor=1.75, implicit=True):
+                 factor=1.75, implicit=True, anderson=0):
     """Cycles until the finest velocity residual (checked at the start of
-    each cycle) is below tol.  Returns (U, cycles, residual, converged)."""
+    each cycle) is below tol, optionally with Anderson mixing of memory
+    `anderson` over the cycles.  Returns (U, cycles, residual, converged)."""
     p = schedule[0][0]
     d = levels[p].mesh.d
     g, a0dt = bdf_forcing(Un, Unm1, dt, bdf_order, d)
     U = np.array(U0, dtype=np.float64, copy=True)
+    mix = Anderson(anderson)
     n = 0
     res = fine_residual(levels[p], U, g, a0dt)
     while res >= tol and n < max_cycles:
-        U = cycle(levels, U, g, a0dt, dtau, schedule, factor, implicit)
+        U = mix.step(U, cycle(levels, U, g, a0dt, dtau, schedule, factor, implicit))
         n += 1
         res = fine_residual(levels[p], U, g, a0dt)
     return U, n, res, res < tol

@@ -27,7 +27,9 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", 
            "fr_pseudo_solve", "fr_dual_init", "fr_dual_step", "fr_dual_velocity", "fr_dual_copy",
            "fr_mlp_create", "fr_mlp_destroy", "fr_mlp_info", "fr_mlp_collect", "fr_mlp_loss_grad",
            "fr_mlp_train", "fr_mlp_predict", "fr_mlp_predict_for", "fr_mlp_params", "fr_gemm_bf16",
-           "fr_mlp_train_step", "fr_mlp_save", "fr_mlp_load", "fr_fma_probe"]
+           "fr_mlp_train_step", "fr_mlp_save", "fr_mlp_load", "fr_fma_probe",
+           "fr_pmg_create", "fr_pmg_destroy", "fr_pmg_set_cycle", "fr_pmg_set_dtau",
+           "fr_pmg_solve", "fr_pmg_set_anderson"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -39,7 +41,8 @@ class fr_dual_opts(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("dtau", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int), ("guess", ctypes.c_int),
                 ("refine", ctypes.c_void_p), ("U_refine", ctypes.c_void_p),
-                ("tol_switch", ctypes.c_double), ("mlp", ctypes.c_void_p)]
+                ("tol_switch", ctypes.c_double), ("mlp", ctypes.c_void_p),
+                ("pmg", ctypes.c_void_p), ("refine_pmg", ctypes.c_void_p)]
 
 
 class fr_dual_stats(ctypes.Structure):
@@ -100,6 +103,13 @@ def _lib():
         lib.fr_mlp_params.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float), sz, i32]
         lib.fr_mlp_train_step.argtypes = [vp, dbl, dp, vp]
         lib.fr_fma_probe.argtypes = [i32, i32, vp, dp, vp]
+        lib.fr_pmg_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        lib.fr_pmg_destroy.argtypes = [vp]
+        lib.fr_pmg_destroy.restype = None
+        lib.fr_pmg_set_cycle.argtypes = [vp, i32, ip, ip]
+        lib.fr_pmg_set_dtau.argtypes = [vp, dp, i32]
+        lib.fr_pmg_set_anderson.argtypes = [vp, i32]
+        lib.fr_pmg_solve.argtypes = [vp, vp, vp, vp, vp, dbl, i32, dbl, dbl, i32, dbl, ip, dp, vp]
         lib.fr_mlp_save.argtypes = [vp, ctypes.c_char_p]
         lib.fr_mlp_load.argtypes = [vp, ctypes.c_char_p, i32, ctypes.POINTER(vp)]
         lib.fr_gemm_bf16.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.c_longlong, vp,
@@ -109,7 +119,8 @@ def _lib():
         lib.fr_last_error.argtypes = []
         lib.fr_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("fr_destroy", "fr_strerror", "fr_last_error", "fr_mlp_destroy"):
+            if name not in ("fr_destroy", "fr_strerror", "fr_last_error", "fr_mlp_destroy",
+                            "fr_pmg_destroy"):
                 getattr(lib, name).restype = i32
         _LIB = lib
     return _LIB
@@ -241,17 +252,65 @@ def fr_pseudo_solve(ctx, U, V, Vn, Vnm1, dt, bdf_order, dtau, tol, max_iter, che
     return st, it.value, res.value
 
 
+def fr_pmg_create(ctx, coarsest_order=1):
+    out = ctypes.c_void_p()
+    _check(_lib().fr_pmg_create(ctypes.c_void_p(ctx), int(coarsest_order), ctypes.byref(out)),
+           "fr_pmg_create")
+    return out.value
+
+
+def fr_pmg_destroy(pmg):
+    _lib().fr_pmg_destroy(ctypes.c_void_p(pmg))
+
+
+def fr_pmg_set_cycle(pmg, schedule):
+    """schedule: list of (order, iterations)."""
+    n = len(schedule)
+    orders = (ctypes.c_int * n)(*[int(o) for o, _ in schedule])
+    iters = (ctypes.c_int * n)(*[int(k) for _, k in schedule])
+    _check(_lib().fr_pmg_set_cycle(ctypes.c_void_p(pmg), n, orders, iters), "fr_pmg_set_cycle")
+
+
+def fr_pmg_set_dtau(pmg, factors=None, implicit=True):
+    """factors: {order: multiplier} or None (keep)."""
+    arr = None
+    if factors is not None:
+        vals = [1.0] * 8
+        for q, f in factors.items():
+            vals[int(q)] = float(f)
+        arr = (ctypes.c_double * 8)(*vals)
+    _check(_lib().fr_pmg_set_dtau(ctypes.c_void_p(pmg), arr, int(bool(implicit))),
+           "fr_pmg_set_dtau")
+
+
+def fr_pmg_set_anderson(pmg, memory):
+    _check(_lib().fr_pmg_set_anderson(ctypes.c_void_p(pmg), int(memory)), "fr_pmg_set_anderson")
+
+
+def fr_pmg_solve(pmg, U, V, Vn, Vnm1, dt, bdf_order, dtau, tol, max_cycles, stall=0.0,
+                 stream=None, allow_noconv=False):
+    """Returns (status, cycles, residual)."""
+    cyc, res = ctypes.c_int(), ctypes.c_double()
+    st = _lib().fr_pmg_solve(ctypes.c_void_p(pmg), _ptr(U), _ptr(V), _ptr(Vn),
+                             _ptr(Vnm1) if Vnm1 is not None else None, float(dt), int(bdf_order),
+                             float(dtau), float(tol), int(max_cycles), float(stall),
+                             ctypes.byref(cyc), ctypes.byref(res), _stream(stream))
+    if not (st == FR_OK or (allow_noconv and st == FR_ENOCONV)):
+        _check(st, "fr_pmg_solve")
+    return st, cyc.value, res.value
+
+
 def fr_dual_init(ctx, U, stream=None):
     _check(_lib().fr_dual_init(ctypes.c_void_p(ctx), _ptr(U), _stream(stream)), "fr_dual_init")
 
 
 def fr_dual_step(ctx, U, dt, dtau, tol, max_iter, check_every=1, guess=FR_GUESS_EXTRAPOLATE,
                  refine=None, U_refine=None, tol_switch=0.0, mlp=None, stream=None,
-                 allow_noconv=False):
+                 allow_noconv=False, pmg=None, refine_pmg=None):
     """Returns (status, fr_dual_stats)."""
     opts = fr_dual_opts(float(dt), float(dtau), float(tol), int(max_iter), int(check_every),
                         int(guess), refine, U_refine.data_ptr() if U_refine is not None else None,
-                        float(tol_switch), mlp)
+                        float(tol_switch), mlp, pmg, refine_pmg)
     stats = fr_dual_stats()
     st = _lib().fr_dual_step(ctypes.c_void_p(ctx), _ptr(U), ctypes.byref(opts),
                              ctypes.byref(stats), _stream(stream))

@@ -259,6 +259,10 @@ int ensure_history(fr_ctx* c) {
 
 }  // namespace
 
+int acmhd::ensure_rk_registers(fr_ctx* c) { return ensure_rk(c); }
+int acmhd::ensure_dual_registers(fr_ctx* c) { return ensure_dual(c); }
+int acmhd::status_of(cudaError_t e, const char* where) { return cuda_status(e, where); }
+
 void acmhd::fill_const(const fr_ctx* c, FrConst<float>* k) { fill_const_t(c, k); }
 void acmhd::fill_const(const fr_ctx* c, FrConst<double>* k) { fill_const_t(c, k); }
 
@@ -651,18 +655,27 @@ int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, 
   // iterations in this context's precision; with a refinement context they
   // stop at tol_switch or when the residual stalls
   const double tol1 = rf ? (o->tol > o->tol_switch ? o->tol : o->tol_switch) : o->tol;
-  int solve = fr_pseudo_solve(c, U, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
-                              o->dtau, tol1, o->max_iter, o->check_every, rf ? 0.99 : 0.0,
-                              &stats.iters, &stats.res, stream);
+  int solve =
+      o->pmg ? fr_pmg_solve(o->pmg, U, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
+                            o->dtau, tol1, o->max_iter, rf ? 0.99 : 0.0, &stats.iters, &stats.res,
+                            stream)
+             : fr_pseudo_solve(c, U, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
+                               o->dtau, tol1, o->max_iter, o->check_every, rf ? 0.99 : 0.0,
+                               &stats.iters, &stats.res, stream);
   if (solve != FR_OK && solve != FR_ENOCONV) return solve;
   stats.res_switch = stats.res;
   if (rf && !(stats.res < o->tol) && stats.iters < o->max_iter) {
     st = cuda_status(acmhd::launch_convert(c, n, c->precision, U, FR_F64, o->U_refine, s),
                      "widen state");
     if (st != FR_OK) return st;
-    solve = fr_pseudo_solve(rf, o->U_refine, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt,
-                            order, o->dtau, o->tol, o->max_iter - stats.iters, o->check_every,
-                            0.0, &stats.iters_refine, &stats.res, stream);
+    solve = o->refine_pmg
+                ? fr_pmg_solve(o->refine_pmg, o->U_refine, c->dual_v, c->hist_v[h0],
+                               c->hist_v[h1], o->dt, order, o->dtau, o->tol,
+                               o->max_iter - stats.iters, 0.0, &stats.iters_refine, &stats.res,
+                               stream)
+                : fr_pseudo_solve(rf, o->U_refine, c->dual_v, c->hist_v[h0], c->hist_v[h1],
+                                  o->dt, order, o->dtau, o->tol, o->max_iter - stats.iters,
+                                  o->check_every, 0.0, &stats.iters_refine, &stats.res, stream);
     if (solve != FR_OK && solve != FR_ENOCONV) return solve;
     st = cuda_status(acmhd::launch_convert(c, n, FR_F64, o->U_refine, c->precision, U, s),
                      "narrow state");

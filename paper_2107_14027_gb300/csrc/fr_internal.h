@@ -134,6 +134,12 @@ namespace acmhd {
 void fill_const(const fr_ctx* c, FrConst<float>* k);
 void fill_const(const fr_ctx* c, FrConst<double>* k);
 
+// Allocate (on first use) a context's RK4 registers / FP64 dual-time
+// registers; map a CUDA status to an FR_* code (recording its text).
+int ensure_rk_registers(fr_ctx* c);
+int ensure_dual_registers(fr_ctx* c);
+int status_of(cudaError_t e, const char* where);
+
 // kernel launchers (defined in the k_*.cu files)
 cudaError_t launch_trace(const fr_ctx* c, const void* U, void* trace, cudaStream_t s);
 cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* trace, void* R,
@@ -151,7 +157,8 @@ cudaError_t launch_widen_velocity(const fr_ctx* c, const void* U, double* V, cud
 cudaError_t launch_bdf_const(const fr_ctx* c, double c1, double c2, const double* Vn,
                              const double* Vnm1, double* C, cudaStream_t s);
 cudaError_t launch_dual_stage(const fr_ctx* c, int stage, double dtau, double a0dt, void* U,
-                              double* V, const double* C, double* partial, cudaStream_t s);
+                              double* V, const double* C, double* partial, cudaStream_t s,
+                              double dV = 1.0, double dA = 1.0);
 cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, int nparts, double count,
                               double* out, cudaStream_t s);
 cudaError_t launch_stage(const fr_ctx* c, const void* U, const void* Tr, const StageArgs& a,

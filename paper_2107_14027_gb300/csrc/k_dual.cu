@@ -63,13 +63,17 @@ bdf_const_kernel(size_t n, double c1, double c2, const double* __restrict__ Vn,
 //   non-velocity rows (T):  as fr_rk_step
 //   velocity rows (FP64):   kv = k + C - (a0/dt) Vin, Vin = V (stage 0) or Vs
 // At stage 0 the sum of kv^2 over real elements goes to partial[blockIdx.x].
+// With point-implicit scaling (P-multigrid smoother), the velocity
+// derivative is multiplied by dV and the gradient rows' by dA before the
+// combination; the residual partial stays that of the unscaled pseudo RHS.
+// dV = dA = 1 leaves every result bit-identical to no scaling.
 template <typename T, int STAGE>
 __global__ void __launch_bounds__(kThreads)
 dual_stage_kernel(size_t n, size_t vel0, size_t nvel, int stride, int ne, double dtau,
-                  double a0dt, T* __restrict__ U, T* __restrict__ Us, T* __restrict__ acc,
-                  const T* __restrict__ k, double* __restrict__ V, double* __restrict__ Vs,
-                  double* __restrict__ Vacc, const double* __restrict__ C,
-                  double* __restrict__ partial) {
+                  double a0dt, double dV, T dA, T* __restrict__ U, T* __restrict__ Us,
+                  T* __restrict__ acc, const T* __restrict__ k, double* __restrict__ V,
+                  double* __restrict__ Vs, double* __restrict__ Vacc,
+                  const double* __restrict__ C, double* __restrict__ partial) {
   __shared__ double red[kThreads];
   const double c = (STAGE == 2) ? dtau : (STAGE == 3 ? dtau / 6.0 : 0.5 * dtau);
   const T ct = static_cast<T>(c);
@@ -78,7 +82,7 @@ dual_stage_kernel(size_t n, size_t vel0, size_t nvel, int stride, int ne, double
        i += (size_t)gridDim.x * kThreads) {
     const bool vel = i >= vel0 && i < vel0 + nvel;
     if (!vel) {
-      const T kk = k[i];
+      const T kk = (i >= vel0 + nvel) ? dA * k[i] : k[i];
       if (STAGE == 3) {
         U[i] = fma(ct, acc[i] + kk, U[i]);
       } else {
@@ -89,8 +93,9 @@ dual_stage_kernel(size_t n, size_t vel0, size_t nvel, int stride, int ne, double
     }
     const size_t j = i - vel0;
     const double vin = (STAGE == 0) ? V[j] : Vs[j];
-    const double kv = static_cast<double>(k[i]) + fma(-a0dt, vin, C[j]);
-    if (STAGE == 0 && (int)(j % (size_t)stride) < ne) sq = fma(kv, kv, sq);
+    const double kv0 = static_cast<double>(k[i]) + fma(-a0dt, vin, C[j]);
+    if (STAGE == 0 && (int)(j % (size_t)stride) < ne) sq = fma(kv0, kv0, sq);
+    const double kv = dV * kv0;
     if (STAGE == 3) {
       const double vn = fma(c, Vacc[j] + kv, V[j]);
       V[j] = vn;
@@ -183,7 +188,8 @@ cudaError_t launch_bdf_const(const fr_ctx* c, double c1, double c2, const double
 
 template <typename T>
 cudaError_t dual_stage_t(const fr_ctx* c, int stage, double dtau, double a0dt, void* U,
-                         double* V, const double* C, double* partial, cudaStream_t s) {
+                         double* V, const double* C, double* partial, double dV, double dA,
+                         cudaStream_t s) {
   const size_t n = (size_t)c->nv * c->npts * c->stride;
   const size_t vel0 = (size_t)c->npts * c->stride;
   const size_t nvel = (size_t)c->dim * c->npts * c->stride;
@@ -196,8 +202,8 @@ cudaError_t dual_stage_t(const fr_ctx* c, int stage, double dtau, double a0dt, v
   double* va = c->dual_vacc;
   const int st = static_cast<int>(c->stride);
 #define ACMHD_STAGE(S)                                                                      \
-  dual_stage_kernel<T, S><<<nb, kThreads, 0, s>>>(n, vel0, nvel, st, c->ne, dtau, a0dt, u, \
-                                                  us, a, k, V, vs, va, C, partial)
+  dual_stage_kernel<T, S><<<nb, kThreads, 0, s>>>(n, vel0, nvel, st, c->ne, dtau, a0dt, dV, \
+                                                  (T)dA, u, us, a, k, V, vs, va, C, partial)
   switch (stage) {
     case 0: ACMHD_STAGE(0); break;
     case 1: ACMHD_STAGE(1); break;
@@ -210,9 +216,11 @@ cudaError_t dual_stage_t(const fr_ctx* c, int stage, double dtau, double a0dt, v
 }
 
 cudaError_t launch_dual_stage(const fr_ctx* c, int stage, double dtau, double a0dt, void* U,
-                              double* V, const double* C, double* partial, cudaStream_t s) {
-  return c->precision == FR_F32 ? dual_stage_t<float>(c, stage, dtau, a0dt, U, V, C, partial, s)
-                                : dual_stage_t<double>(c, stage, dtau, a0dt, U, V, C, partial, s);
+                              double* V, const double* C, double* partial, cudaStream_t s,
+                              double dV, double dA) {
+  return c->precision == FR_F32
+             ? dual_stage_t<float>(c, stage, dtau, a0dt, U, V, C, partial, dV, dA, s)
+             : dual_stage_t<double>(c, stage, dtau, a0dt, U, V, C, partial, dV, dA, s);
 }
 
 cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, int nparts, double count,

@@ -130,3 +130,28 @@ def test_schedule_must_move_by_one_order():
     g = np.zeros_like(U0)
     with pytest.raises(ValueError):
         pmg.cycle(levels, U0, g, 100.0, 1e-3, [(3, 1), (1, 2), (3, 1)], 1.75)
+
+
+def test_anderson_terminates_on_a_linear_map():
+    """On x <- M x + b in dimension n, Anderson mixing with memory >= n
+    reaches the fixed point within n + 1 steps (it is GMRES on (I - M) x = b
+    for linear maps), while the plain iteration is still far from it."""
+    rng = np.random.default_rng(3)
+    n = 6
+    Q = np.linalg.qr(rng.normal(size=(n, n)))[0]
+    M = Q @ np.diag(np.linspace(0.5, 0.99, n)) @ Q.T
+    b = rng.normal(size=n)
+    xs = np.linalg.solve(np.eye(n) - M, b)
+    mix = pmg.Anderson(n)
+    x = np.zeros(n)
+    for _ in range(n + 1):
+        x = mix.step(x, M @ x + b)
+    assert np.linalg.norm(x - xs) < 1e-9 * np.linalg.norm(xs)
+    y = np.zeros(n)
+    plain = pmg.Anderson(0)
+    for _ in range(n + 1):
+        y = plain.step(y, M @ y + b)
+    # m = 0 is the plain iteration: from 0, x_{n+1} = sum_{k<=n} M^k b
+    np.testing.assert_allclose(y, sum(np.linalg.matrix_power(M, k) @ b for k in range(n + 1)),
+                               rtol=1e-13)
+    assert np.linalg.norm(y - xs) > 1e-2 * np.linalg.norm(xs)
