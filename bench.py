@@ -553,129 +553,240 @@ def _fma_peak(abi, precision, stream, torch):
     return flops / t
 
 
+class _DualSolver:
+    """One dual-time solver of the 3-D Taylor-Green workload: the stepping
+    context (FP32 unless --dual-precision 64), an FP64 twin for the stretch
+    below the FP32 rounding floor, and their pseudo solvers (P-multigrid
+    cycles, with Anderson mixing in the FP64 phase, unless --dual-solver
+    rk4)."""
+
+    def __init__(self, abi, args, prec, U0, n, lo, hi, order):
+        self.abi, self.args, self.prec = abi, args, prec
+        zeta, nu, t_r = 2.5, 1.0 / 1600.0, 5e-3
+        self.refine = prec == abi.FR_F32 and args.dual_tol < _TOL_SWITCH
+        self.c = abi.fr_create(n, lo, hi, order, 13, zeta, nu, t_r, prec)
+        self.c64 = abi.fr_create(n, lo, hi, order, 13, zeta, nu, t_r, abi.FR_F64) if self.refine \
+            else None
+        self.U = abi.pack_state(self.c, U0, prec)
+        self.U64 = abi.new_state(self.c64, abi.FR_F64) if self.refine else None
+        self.pm = [None, None]
+        if args.dual_solver != "rk4":
+            factors = None
+            if args.dual_pmg_factors:
+                fs = [float(x) for x in args.dual_pmg_factors.split(",")]
+                factors = {order - i: f for i, f in enumerate(fs)}
+            for j, c in enumerate((self.c, self.c64)):
+                if c is None:
+                    continue
+                self.pm[j] = abi.fr_pmg_create(c, 1)
+                abi.fr_pmg_set_dtau(self.pm[j], factors, True)
+                last = j == 1 or not self.refine
+                if args.dual_solver == "pmg-aa" and last:
+                    abi.fr_pmg_set_anderson(self.pm[j], args.dual_anderson)
+
+    def step(self, dt, guess, cap, mlp=None):
+        """One physical step; returns (status, stats, wall seconds)."""
+        import torch
+        a = self.args
+        if a.dual_solver != "rk4":
+            cap = max(1, cap // a.dual_pmg_iters_per_cycle)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, s = self.abi.fr_dual_step(self.c, self.U, dt, a.dual_dtau, a.dual_tol, cap,
+                                      check_every=5, guess=guess, refine=self.c64,
+                                      U_refine=self.U64, tol_switch=_TOL_SWITCH, mlp=mlp,
+                                      allow_noconv=True, pmg=self.pm[0], refine_pmg=self.pm[1])
+        torch.cuda.synchronize()
+        return st, s, time.perf_counter() - t0
+
+    def destroy(self):
+        for x in self.pm:
+            if x is not None:
+                self.abi.fr_pmg_destroy(x)
+        self.abi.fr_destroy(self.c)
+        if self.c64 is not None:
+            self.abi.fr_destroy(self.c64)
+
+
+_TOL_SWITCH = 5e-6
+
+
+def _dual_case(args):
+    n, order = (args.dual_mesh,) * 3, args.dual_order
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    return n, order, lo, hi
+
+
+def _dual_config(args, workload, extra):
+    cfg = {"workload": workload, "order": args.dual_order, "mesh": [args.dual_mesh] * 3,
+           "dt": 1e-2, "bdf": 2, "tol": args.dual_tol, "tol_switch": _TOL_SWITCH,
+           "dtau": args.dual_dtau, "solver": args.dual_solver,
+           "pseudo": {"rk4": "classical RK4, fixed dtau (iters = RK4 steps)",
+                      "pmg": "P-multigrid cycles p..1 (iters = cycles)",
+                      "pmg-aa": "P-multigrid cycles p..1, Anderson mixing in the FP64 phase "
+                                "(iters = cycles)"}[args.dual_solver],
+           "anderson": args.dual_anderson if args.dual_solver == "pmg-aa" else 0,
+           "pmg_factors": args.dual_pmg_factors or "1.75^(p-q)"}
+    cfg.update(extra)
+    return cfg
+
+
+def _rec(k, st, s, wall):
+    return {"step": k, "wall_s": wall, "iters": s.iters, "iters_fp64": s.iters_refine,
+            "res": s.res, "res_switch": s.res_switch, "guess": s.guess_used,
+            "res_guess": list(s.res_guess), "converged": st == 0}
+
+
 def run_dual(args):
-    """Dual time stepping on the 3-D p = 4, 48^3 Taylor-Green workload: BDF2
-    physical steps dt = 1e-2, RK4 pseudo steps dtau = 1e-3 to an FP64 velocity
-    residual of --dual-tol (1e-6); FP32 RHS, handing over to an FP64 twin at the
-    FP32 floor when the tolerance lies below it.  --dual-order, --dual-mesh,
-    --dual-dtau and --dual-precision 64 (FP64 throughout, no twin) select
-    other cases of the same problem.
-    Solver A runs the first steps with the plain extrapolated guess while
-    element samples are collected and the network is trained; then a fork B
-    of A (identical history) takes the held-out steps with the learned guess
-    and A with the plain one.  Metric: wall-seconds per held-out physical step
-    (host clock around fr_dual_step, device synchronised)."""
+    """Learned vs plain initial guess on the dual-time workload (3-D p = 4,
+    48^3 Taylor-Green, BDF2 dt = 1e-2, FP32 RHS with an FP64 twin below the
+    FP32 floor, residual tolerance --dual-tol = 1e-6).  Solver A takes 3
+    steps, then --dual-collect-steps more while element samples are
+    collected; the network is trained (newest 10 % of the samples held out
+    for validation, Adam with decoupled weight decay, the epoch count with
+    the lowest validation loss kept by saving and reloading the network);
+    then a fork B of A (same history) takes the held-out steps with the
+    learned guess while A takes them with the plain extrapolation.  Metric:
+    wall-seconds per held-out physical step (host clock around
+    fr_dual_step, device synchronised)."""
+    import tempfile
     import torch
     from paper_2107_14027_gb300 import abi
     from paper_2107_14027_gb300 import workloads as W
-    n, order, nv, d = (args.dual_mesh,) * 3, args.dual_order, 13, 3
-    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
-    zeta, nu, t_r = 2.5, 1.0 / 1600.0, 5e-3
-    dt, dtau, tol, tol_switch = 1e-2, args.dual_dtau, args.dual_tol, 5e-6
+    n, order, lo, hi = _dual_case(args)
     prec = abi.FR_F64 if args.dual_precision == 64 else abi.FR_F32
-    refine = prec == abi.FR_F32 and args.dual_tol < tol_switch
+    U0 = W.taylor_green(n, lo, hi, order, dtype=np.float32 if prec == abi.FR_F32 else np.float64)
+    A = _DualSolver(abi, args, prec, U0, n, lo, hi, order)
+    B = _DualSolver(abi, args, prec, U0, n, lo, hi, order)
     n_warm, n_collect, n_held = 3, args.dual_collect_steps, args.dual_held_steps
     per_step = max(1, args.dual_samples // n_collect)
-    U0 = W.taylor_green(n, lo, hi, order, dtype=np.float32 if prec == abi.FR_F32 else np.float64)
-    solvers, pmgs = [], []
-    factors = None
-    if args.dual_pmg_factors:
-        fs = [float(x) for x in args.dual_pmg_factors.split(",")]
-        factors = {order - i: f for i, f in enumerate(fs)}
-    for _ in range(2):
-        c32 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, prec)
-        c64 = abi.fr_create(n, lo, hi, order, nv, zeta, nu, t_r, abi.FR_F64) if refine else None
-        solvers.append([c32, c64, abi.pack_state(c32, U0, prec),
-                        abi.new_state(c64, abi.FR_F64) if refine else None])
-        pm = [None, None]
-        if args.dual_pmg:
-            for j, c in enumerate((c32, c64)):
-                if c is None:
-                    continue
-                pm[j] = abi.fr_pmg_create(c, 1)
-                abi.fr_pmg_set_dtau(pm[j], factors, not args.dual_pmg_explicit)
-                if args.dual_anderson and (j == 1 or not refine or args.dual_anderson_fp32):
-                    abi.fr_pmg_set_anderson(pm[j], args.dual_anderson)
-                if args.dual_pmg_bottom or args.dual_pmg_top:
-                    sched = [(q, 1) for q in range(order, 1, -1)] + [(1, args.dual_pmg_bottom or 4)]
-                    sched += [(q, 1) for q in range(2, order)] + [(order, args.dual_pmg_top or 7)]
-                    abi.fr_pmg_set_cycle(pm[j], sched)
-        pmgs.append(pm)
-    abi.fr_dual_init(solvers[0][0], solvers[0][2])
-    net = abi.fr_mlp_create(solvers[0][0], args.dual_hidden, per_step * n_collect, seed=2021)
+    cap_samples = per_step * n_collect
+    abi.fr_dual_init(A.c, A.U)
+    net = abi.fr_mlp_create(A.c, args.dual_hidden, cap_samples, seed=2021)
     log = {"A": [], "B": []}
 
-    def step(k, which, guess, max_iter):
-        c32, c64, U, U64 = solvers[which]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pm = pmgs[which]
-        cap = max(1, max_iter // args.dual_pmg_iters_per_cycle) if args.dual_pmg else max_iter
-        st, s = abi.fr_dual_step(c32, U, dt, dtau, tol, cap, check_every=5, guess=guess,
-                                 refine=c64 if refine else None,
-                                 U_refine=U64 if refine else None, tol_switch=tol_switch,
-                                 mlp=net, allow_noconv=True, pmg=pm[0], refine_pmg=pm[1])
-        torch.cuda.synchronize()
-        rec = {"step": k, "wall_s": time.perf_counter() - t0, "iters_fp32": s.iters,
-               "iters_fp64": s.iters_refine, "res": s.res, "res_switch": s.res_switch,
-               "guess": s.guess_used, "res_guess": list(s.res_guess), "converged": st == 0}
-        log["AB"[which]].append(rec)
-        print(json.dumps({"solver": "AB"[which], **rec}), file=sys.stderr, flush=True)
+    def step(S, name, k, guess, cap, mlp=None):
+        st, s, wall = S.step(1e-2, guess, cap, mlp)
+        rec = _rec(k, st, s, wall)
+        log[name].append(rec)
+        print(json.dumps({"solver": name, **rec}), file=sys.stderr, flush=True)
 
     k = 0
     for _ in range(n_warm + n_collect):
         k += 1
-        step(k, 0, abi.FR_GUESS_EXTRAPOLATE, args.dual_train_iters)
+        step(A, "A", k, abi.FR_GUESS_EXTRAPOLATE, args.dual_train_iters)
         if k > n_warm:
             abi.fr_mlp_collect(net, per_step, seed=1000 + k)
+    # training: newest 10 % held out; keep the epoch count with the lowest
+    # validation loss (saved and reloaded)
+    n_val = max(1, cap_samples // 10)
+    abi.fr_mlp_set_training(net, n_val, args.dual_wd)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    curve, best = [], (float("inf"), 0)
+    path = os.path.join(tempfile.mkdtemp(prefix="acmhd_mlp_"), "best.bin")
     loss0 = abi.fr_mlp_train(net, 1, args.dual_lr)
-    loss = abi.fr_mlp_train(net, args.dual_epochs - 1, args.dual_lr)
+    done = 1
+    while done < args.dual_epochs:
+        chunk = min(args.dual_val_every, args.dual_epochs - done)
+        tl = abi.fr_mlp_train(net, chunk, args.dual_lr)
+        done += chunk
+        vl = abi.fr_mlp_validation_loss(net)
+        curve.append({"epochs": done, "train_loss": tl, "val_loss": vl})
+        if vl < best[0]:
+            best = (vl, done)
+            abi.fr_mlp_save(net, path)
+    if os.path.exists(path):
+        abi.fr_mlp_destroy(net)
+        net = abi.fr_mlp_load(A.c, path, capacity=1)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    abi.fr_dual_copy(solvers[1][0], solvers[0][0])
+    abi.fr_dual_copy(B.c, A.c)
     for _ in range(n_held):
         k += 1
-        step(k, 0, abi.FR_GUESS_EXTRAPOLATE, args.dual_held_iters)
-        step(k, 1, abi.FR_GUESS_MLP, args.dual_held_iters)
+        step(A, "A", k, abi.FR_GUESS_EXTRAPOLATE, args.dual_held_iters)
+        step(B, "B", k, abi.FR_GUESS_MLP, args.dual_held_iters, net)
     wa = float(np.mean([r["wall_s"] for r in log["A"][-n_held:]]))
     wb = float(np.mean([r["wall_s"] for r in log["B"]]))
-    Va = abi.new_velocity(solvers[0][0], d, order)
-    Vb = abi.new_velocity(solvers[1][0], d, order)
-    abi.fr_dual_velocity(solvers[0][0], Va)
-    abi.fr_dual_velocity(solvers[1][0], Vb)
+    d = 3
+    Va, Vb = abi.new_velocity(A.c, d, order), abi.new_velocity(B.c, d, order)
+    abi.fr_dual_velocity(A.c, Va)
+    abi.fr_dual_velocity(B.c, Vb)
     dv = float((Va - Vb).abs().max().item())
     out = {
-        "metric": f"wall-s per physical step at {tol:g} residual", "value": wb, "unit": "s",
-        "higher_is_better": False, "n_gpus": 1,
+        "metric": f"wall-s per physical step at {args.dual_tol:g} residual", "value": wb,
+        "unit": "s", "higher_is_better": False, "n_gpus": 1,
         "dtype": "f64" if prec == abi.FR_F64 else "f32+f64", "data": "synthetic",
-        "config": {"workload": f"hex_p{order}_{args.dual_mesh}cube_dual", "order": order,
-                   "mesh": list(n), "dt": dt, "dtau": dtau, "tol": tol,
-                   "tol_switch": tol_switch, "bdf": 2,
-                   "pseudo": ("P-multigrid cycles (iters count cycles)" if args.dual_pmg
-                              else "RK4"),
-                   "pmg_factors": args.dual_pmg_factors, "pmg_implicit": not args.dual_pmg_explicit,
-                   "anderson": args.dual_anderson, "anderson_fp32": args.dual_anderson_fp32,
-                   "max_iter_train_steps": args.dual_train_iters,
-                   "max_iter_held_steps": args.dual_held_iters,
-                   "mlp": {"hidden": args.dual_hidden, "samples": per_step * n_collect,
-                           "epochs": args.dual_epochs, "lr": args.dual_lr, "train_s": t_train,
-                           "loss_first": loss0, "loss_last": loss}},
+        "config": _dual_config(args, f"hex_p{order}_{args.dual_mesh}cube_dual", {
+            "max_iter_train_steps": args.dual_train_iters,
+            "max_iter_held_steps": args.dual_held_iters,
+            "mlp": {"hidden": args.dual_hidden, "samples": cap_samples, "validation": n_val,
+                    "epochs": args.dual_epochs, "best_epochs": best[1], "lr": args.dual_lr,
+                    "weight_decay": args.dual_wd, "train_s": t_train, "loss_first": loss0,
+                    "curve": curve}}),
         "plain_wall_s": wa, "learned_wall_s": wb, "speedup": wa / wb,
         "held_out_steps": n_held, "max_velocity_difference": dv,
         "steps": {"plain": log["A"], "learned": log["B"]},
     }
     print(json.dumps(out))
-    for pm in pmgs:
-        for x in pm:
-            if x is not None:
-                abi.fr_pmg_destroy(x)
-    for c32, c64, _, _ in solvers:
-        abi.fr_destroy(c32)
-        if c64 is not None:
-            abi.fr_destroy(c64)
     abi.fr_mlp_destroy(net)
+    A.destroy()
+    B.destroy()
+
+
+def run_dual_steps(args):
+    """--dual-steps physical steps of the dual-time workload with the plain
+    extrapolated guess (BASELINE's 200-step run), pseudo-iterations and
+    wall-seconds per step logged; for the first --dual-fp64-ref steps an
+    FP64-only solver (FP64 RHS, same solver otherwise) runs the same steps
+    from the same initial state and the largest velocity difference between
+    the two is logged: the error of the FP32 + FP64-twin result against an
+    FP64 run."""
+    import torch
+    from paper_2107_14027_gb300 import abi
+    from paper_2107_14027_gb300 import workloads as W
+    n, order, lo, hi = _dual_case(args)
+    U0 = W.taylor_green(n, lo, hi, order, dtype=np.float32)
+    S = _DualSolver(abi, args, abi.FR_F32, U0, n, lo, hi, order)
+    abi.fr_dual_init(S.c, S.U)
+    R = None
+    if args.dual_fp64_ref > 0:
+        R = _DualSolver(abi, args, abi.FR_F64, U0.astype(np.float64), n, lo, hi, order)
+        abi.fr_dual_init(R.c, R.U)
+    d = 3
+    V, Vr = abi.new_velocity(S.c, d, order), (abi.new_velocity(R.c, d, order) if R else None)
+    log = []
+    for k in range(1, args.dual_steps + 1):
+        st, s, wall = S.step(1e-2, abi.FR_GUESS_EXTRAPOLATE, args.dual_held_iters)
+        rec = _rec(k, st, s, wall)
+        if R is not None and k <= args.dual_fp64_ref:
+            st64, s64, wall64 = R.step(1e-2, abi.FR_GUESS_EXTRAPOLATE, args.dual_held_iters)
+            abi.fr_dual_velocity(S.c, V)
+            abi.fr_dual_velocity(R.c, Vr)
+            rec["fp64_ref"] = {"converged": st64 == 0, "iters": s64.iters, "wall_s": wall64,
+                               "res": s64.res,
+                               "max_velocity_error": float((V - Vr).abs().max().item()),
+                               "rms_velocity_error": float(torch.sqrt(((V - Vr) ** 2).mean()))}
+        log.append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+    walls = [r["wall_s"] for r in log]
+    out = {
+        "metric": f"wall-s per physical step at {args.dual_tol:g} residual",
+        "value": float(np.mean(walls)), "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": _dual_config(args, f"hex_p{order}_{args.dual_mesh}cube_dual_steps",
+                               {"steps": args.dual_steps, "fp64_reference_steps": args.dual_fp64_ref,
+                                "max_iter": args.dual_held_iters}),
+        "converged_steps": int(sum(r["converged"] for r in log)),
+        "total_wall_s": float(np.sum(walls)),
+        "max_fp64_velocity_error": max([r["fp64_ref"]["max_velocity_error"] for r in log
+                                        if "fp64_ref" in r] or [None]),
+        "steps": log,
+    }
+    print(json.dumps(out))
+    S.destroy()
+    if R is not None:
+        R.destroy()
 
 
 def run_profile_case(args):
@@ -717,11 +828,15 @@ def run_sweep(args):
         nside = W.ORDER_SWEEP_MESH[order]
         n = (nside,) * 3
         lo, hi = (-np.pi,) * 3, (np.pi,) * 3
-        U = W.taylor_green(n, lo, hi, order, dtype=np.float32)
-        ctx = abi.fr_create(n, lo, hi, order, 13, 2.5, 1 / 1600, 5e-3, abi.FR_F32, 0)
+        prec = abi.FR_F64 if args.sweep_precision == 64 else abi.FR_F32
+        nside = args.sweep_mesh or nside
+        n = (nside,) * 3
+        U = W.taylor_green(n, lo, hi, order,
+                           dtype=np.float64 if prec == abi.FR_F64 else np.float32)
+        ctx = abi.fr_create(n, lo, hi, order, 13, 2.5, 1 / 1600, 5e-3, prec, 0)
         stride, ne, nbytes = abi.fr_layout(ctx)
-        Ud = abi.pack_state(ctx, U, abi.FR_F32)
-        Rd = abi.new_state(ctx, abi.FR_F32)
+        Ud = abi.pack_state(ctx, U, prec)
+        Rd = abi.new_state(ctx, prec)
         K, Wm = args.steps, args.warmup
         t_rhs = _time_loop(lambda: abi.fr_rhs(ctx, Ud, Rd, stream), stream, K, Wm, torch) / K
         t_tr = _time_loop(lambda: abi.fr_trace(ctx, Ud, stream), stream, K, Wm, torch) / K
@@ -737,14 +852,17 @@ def run_sweep(args):
         dof = ne * m ** 3 * 13
         # own minimum of the two-kernel RHS: U read once, R written once, the
         # y/z face traces (7 slots, 4 faces) written and read once
-        own = ne * (2 * 13 * m ** 3 + 2 * 4 * 7 * m * m) * 4
+        b = 8 if prec == abi.FR_F64 else 4
+        own = ne * (2 * 13 * m ** 3 + 2 * 4 * 7 * m * m) * b
         rows.append({"order": order, "mesh": nside, "gdof_s": dof / t_rhs / 1e9,
+                     "fused_tflops": ne * m ** 3 * (42 * m + 195) / t_vol / 1e12,
                      "unfused_gdof_s": dof / t_unf / 1e9, "fused_speedup": t_unf / t_rhs,
                      "ms": {"rhs": 1e3 * t_rhs, "trace": 1e3 * t_tr, "volume": 1e3 * t_vol,
                             "unfused": 1e3 * t_unf},
                      "own_min_gb": own / 1e9, "hbm_frac_own": own / t_rhs / 1e9 / peak})
     print(json.dumps({"metric": "GDOF-RHS/s, order sweep, fused vs unfused", "unit": "GDOF/s",
-                      "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "higher_is_better": True, "n_gpus": 1,
+                      "dtype": "f64" if args.sweep_precision == 64 else "f32", "data": "synthetic",
                       "steps": args.steps, "warmup": args.warmup, "peak_gbs": peak,
                       "peak_source": peak_src, "orders": rows}))
 
@@ -842,12 +960,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mesh", type=int, default=None,
                     help="profiling only: run fr_rhs on an N^3 mesh and print its timing")
-    ap.add_argument("--workload", default="rhs", choices=["rhs", "dual", "rk", "sweep", "mlp"],
+    ap.add_argument("--workload", default="rhs",
+                    choices=["rhs", "dual", "dual-steps", "rk", "sweep", "mlp"],
                     help="rhs: the fused RHS (default); dual: BDF2 dual time stepping, "
-                         "plain vs learned initial guess; rk: RK4 pseudo-steps, fused "
+                         "plain vs learned initial guess; dual-steps: N dual-time steps with "
+                         "the plain guess, error against an FP64 run; rk: RK4 pseudo-steps, fused "
                          "stage vs separate update; sweep: orders 1..6, fused vs unfused; "
                          "mlp: the network's tensor-core GEMMs")
     ap.add_argument("--sweep-orders", default="1,2,3,4,5,6")
+    ap.add_argument("--sweep-precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--sweep-mesh", type=int, default=0,
+                    help="elements per direction for every order (default: ~38M points)")
     ap.add_argument("--rk-order", type=int, default=3)
     ap.add_argument("--rk-mesh", type=int, default=None,
                     help="elements per direction (default: the order sweep's mesh)")
@@ -861,27 +984,26 @@ def main():
     ap.add_argument("--dual-held-steps", type=int, default=5)
     ap.add_argument("--dual-samples", type=int, default=5000)
     ap.add_argument("--dual-epochs", type=int, default=400)
-    ap.add_argument("--dual-train-iters", type=int, default=200,
+    ap.add_argument("--dual-train-iters", type=int, default=1200,
                     help="pseudo-iteration cap of the steps before the held-out ones")
-    ap.add_argument("--dual-held-iters", type=int, default=600,
+    ap.add_argument("--dual-held-iters", type=int, default=1200,
                     help="pseudo-iteration cap of the held-out steps")
-    ap.add_argument("--dual-pmg", action="store_true",
-                    help="P-multigrid cycles for the pseudo-iterations (orders p .. 1)")
+    ap.add_argument("--dual-solver", default="pmg-aa", choices=["rk4", "pmg", "pmg-aa"],
+                    help="pseudo solver: RK4 steps, P-multigrid cycles, or cycles with "
+                         "Anderson mixing in the FP64 phase (default)")
     ap.add_argument("--dual-pmg-factors", default="",
                     help="pseudo-step multipliers for orders p, p-1, .., 1 (default 1.75^(p-q))")
-    ap.add_argument("--dual-pmg-explicit", action="store_true",
-                    help="no point-implicit scaling of the stiff linear terms")
-    ap.add_argument("--dual-pmg-bottom", type=int, default=0,
-                    help="iterations on the coarsest order per cycle (default 4)")
-    ap.add_argument("--dual-pmg-top", type=int, default=0,
-                    help="iterations on the finest order at the end of a cycle (default 7)")
-    ap.add_argument("--dual-anderson", type=int, default=0,
-                    help="Anderson mixing memory over the P-multigrid cycles (FP64 phase)")
-    ap.add_argument("--dual-anderson-fp32", action="store_true",
-                    help="also mix the cycles of the FP32 phase")
+    ap.add_argument("--dual-anderson", type=int, default=8, help="Anderson memory (pmg-aa)")
     ap.add_argument("--dual-pmg-iters-per-cycle", type=int, default=10,
                     help="fine-iteration equivalents of one cycle, to turn the iteration "
                          "caps into cycle caps")
+    ap.add_argument("--dual-wd", type=float, default=1e-2, help="weight decay of the network")
+    ap.add_argument("--dual-val-every", type=int, default=25,
+                    help="epochs between validation-loss checks")
+    ap.add_argument("--dual-steps", type=int, default=200,
+                    help="physical steps of --workload dual-steps")
+    ap.add_argument("--dual-fp64-ref", type=int, default=0,
+                    help="dual-steps: run an FP64-only solver beside for this many steps")
     ap.add_argument("--dual-tol", type=float, default=1e-6,
                     help="residual tolerance; below the FP32 floor (5e-6) an FP64 twin refines")
     args = ap.parse_args()
@@ -893,6 +1015,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "dual":
         run_dual(args)
+    elif args.workload == "dual-steps":
+        run_dual_steps(args)
     elif args.workload == "rk":
         run_rk(args)
     elif args.workload == "sweep":

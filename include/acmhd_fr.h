@@ -246,8 +246,12 @@ int fr_pseudo_solve(fr_ctx* ctx, void* U, double* V, const double* Vn, const dou
  * (also when the solve returns FR_ENOCONV, which is passed on).  U receives
  * the new level.  FR_GUESS_MLP: the extrapolated guess and the network's
  * guess (opts->mlp, three stored levels needed) are both evaluated - one RHS
- * and residual each - and the one with the smaller residual is iterated, so
- * the tolerance decides convergence exactly as without the network.
+ * and residual each - and so is the point of the segment between them,
+ * (1 - alpha) extrapolation + alpha network with alpha in (0, 1) the
+ * minimiser of the linearised residual |r0 + alpha (r1 - r0)| (r0, r1 the
+ * two FP64 velocity residuals; one more RHS and residual).  The candidate
+ * with the smallest residual is iterated, so the tolerance decides
+ * convergence exactly as without the network.
  *
  * Mixed precision: FP32 arithmetic cannot bring the residual below its own
  * rounding floor (the FP32 RHS of the stored state).  With `refine` set to
@@ -340,6 +344,9 @@ typedef struct fr_dual_stats {
     double res_switch;    /* residual when ctx handed over (or final) */
     int guess_used;       /* FR_GUESS_* actually used (the MLP guess falls back) */
     double res_guess[2];  /* FR_GUESS_MLP: initial residual of [extrapolation, network] */
+    double mlp_weight;    /* FR_GUESS_MLP: weight alpha of the network's guess in the
+                             state iterated: 0 extrapolation, 1 network, between: blend */
+    double res_blend;     /* FR_GUESS_MLP: residual of the blend (NaN if not tried) */
 } fr_dual_stats;
 
 int fr_dual_init(fr_ctx* ctx, const void* U, void* stream);
@@ -397,6 +404,16 @@ int fr_mlp_train(fr_mlp* mlp, int epochs, double lr, double* loss, void* stream)
 int fr_mlp_predict(fr_mlp* mlp, void* U, double* V, void* stream);
 int fr_mlp_predict_for(fr_mlp* mlp, fr_ctx* ctx, void* U, double* V, void* stream);
 int fr_mlp_params(fr_mlp* mlp, int which, float* host, size_t count, int set);
+
+/* Training options.  n_val: the newest n_val collected samples are held out
+ * of training (fr_mlp_loss_grad, fr_mlp_train, fr_mlp_train_step use the
+ * others) and fr_mlp_validation_loss reports the loss on them; weight_decay:
+ * decoupled weight decay of Adam (AdamW: every step also subtracts
+ * lr * weight_decay * w from each weight; biases are not decayed).  Both 0
+ * by default.  FR_EINVAL for negative values or n_val beyond the capacity;
+ * training needs at least one training sample. */
+int fr_mlp_set_training(fr_mlp* mlp, int n_val, double weight_decay);
+int fr_mlp_validation_loss(fr_mlp* mlp, double* loss, void* stream);
 
 /* One full-batch Adam step over the collected samples (fr_mlp_train with
  * one epoch); *loss (if non-NULL) is the loss before the step.  Synchronises

@@ -21,7 +21,9 @@ Matrices act on columns: W is (out x in), a batch is stored with samples
 as columns (X is K x B), matching the element-fastest state layout.
 
 Pins (tests/test_oracle_mlp.py): backward against central finite
-differences; a network built to represent a known piecewise-linear map;
+differences; the blend weight of the two guesses minimises a linear
+residual along the segment (brute-force scan); weight decay alone (zero gradient) shrinks the weights by the
+factor 1 - lr * weight_decay per step and leaves the biases; a network built to represent a known piecewise-linear map;
 Adam's first step moves every parameter by lr times the sign of its
 gradient; features/targets reproduce the extrapolation identity on data
 that is quadratic in time.
@@ -63,10 +65,13 @@ def backward(params, cache, Y, Tgt):
 
 
 class Adam:
-    """Adam on a list of (W, b) layers."""
+    """Adam on a list of (W, b) layers; with weight_decay > 0 the decoupled
+    form (AdamW, Loshchilov & Hutter): each step also subtracts
+    lr * weight_decay * W from the weights (not the biases)."""
 
-    def __init__(self, params, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    def __init__(self, params, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
         self.lr, self.b1, self.b2, self.eps = lr, beta1, beta2, eps
+        self.wd = weight_decay
         self.m = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
         self.v = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
         self.t = 0
@@ -82,7 +87,8 @@ class Adam:
                 self.v[i][j] = self.b2 * self.v[i][j] + (1.0 - self.b2) * g * g
                 mh = self.m[i][j] / (1.0 - self.b1 ** self.t)
                 vh = self.v[i][j] / (1.0 - self.b2 ** self.t)
-                layer.append(p - self.lr * mh / (np.sqrt(vh) + self.eps))
+                decay = self.wd * p if j == 0 else 0.0
+                layer.append(p - self.lr * (mh / (np.sqrt(vh) + self.eps) + decay))
             out.append(tuple(layer))
         return out
 
@@ -114,3 +120,15 @@ def apply_guess(Y, Un, Unm1, Unm2, out_scale):
     nv, npts, ne = Un.shape
     t = np.asarray(out_scale, dtype=np.float64)[:, None, None]
     return extrapolate(Un, Unm1, Unm2) + t * Y.reshape(nv, npts, ne)
+
+
+def blend_weight(r0, r1):
+    """Weight alpha in [0, 1] of the network's guess on the segment from the
+    extrapolation (residual r0) to the network's guess (residual r1) that
+    minimises the linearised residual |r0 + alpha (r1 - r0)|_2 (the build's
+    own fallback rule for the learned guess)."""
+    d = np.asarray(r1, dtype=np.float64) - np.asarray(r0, dtype=np.float64)
+    dd = float(np.sum(d * d))
+    if dd == 0.0:
+        return 0.0
+    return float(np.clip(-np.sum(np.asarray(r0) * d) / dd, 0.0, 1.0))

@@ -29,7 +29,8 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", 
            "fr_mlp_train", "fr_mlp_predict", "fr_mlp_predict_for", "fr_mlp_params", "fr_gemm_bf16",
            "fr_mlp_train_step", "fr_mlp_save", "fr_mlp_load", "fr_fma_probe",
            "fr_pmg_create", "fr_pmg_destroy", "fr_pmg_set_cycle", "fr_pmg_set_dtau",
-           "fr_pmg_solve", "fr_pmg_set_anderson"]
+           "fr_pmg_solve", "fr_pmg_set_anderson", "fr_mlp_set_training",
+           "fr_mlp_validation_loss"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -48,7 +49,8 @@ class fr_dual_opts(ctypes.Structure):
 class fr_dual_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("iters_refine", ctypes.c_int), ("res", ctypes.c_double),
                 ("res_switch", ctypes.c_double), ("guess_used", ctypes.c_int),
-                ("res_guess", ctypes.c_double * 2)]
+                ("res_guess", ctypes.c_double * 2), ("mlp_weight", ctypes.c_double),
+                ("res_blend", ctypes.c_double)]
 
 
 class FrError(RuntimeError):
@@ -109,6 +111,8 @@ def _lib():
         lib.fr_pmg_set_cycle.argtypes = [vp, i32, ip, ip]
         lib.fr_pmg_set_dtau.argtypes = [vp, dp, i32]
         lib.fr_pmg_set_anderson.argtypes = [vp, i32]
+        lib.fr_mlp_set_training.argtypes = [vp, i32, dbl]
+        lib.fr_mlp_validation_loss.argtypes = [vp, dp, vp]
         lib.fr_pmg_solve.argtypes = [vp, vp, vp, vp, vp, dbl, i32, dbl, dbl, i32, dbl, ip, dp, vp]
         lib.fr_mlp_save.argtypes = [vp, ctypes.c_char_p]
         lib.fr_mlp_load.argtypes = [vp, ctypes.c_char_p, i32, ctypes.POINTER(vp)]
@@ -381,6 +385,18 @@ def fr_mlp_train(mlp, epochs, lr, stream=None):
     loss = ctypes.c_double()
     _check(_lib().fr_mlp_train(ctypes.c_void_p(mlp), int(epochs), float(lr), ctypes.byref(loss),
                                _stream(stream)), "fr_mlp_train")
+    return loss.value
+
+
+def fr_mlp_set_training(mlp, n_val=0, weight_decay=0.0):
+    _check(_lib().fr_mlp_set_training(ctypes.c_void_p(mlp), int(n_val), float(weight_decay)),
+           "fr_mlp_set_training")
+
+
+def fr_mlp_validation_loss(mlp, stream=None):
+    loss = ctypes.c_double()
+    _check(_lib().fr_mlp_validation_loss(ctypes.c_void_p(mlp), ctypes.byref(loss),
+                                         _stream(stream)), "fr_mlp_validation_loss")
     return loss.value
 
 

@@ -351,7 +351,7 @@ void fr_destroy(fr_ctx* c) {
                   c->dual_vs, c->dual_vacc, c->dual_c, c->dual_partial, c->dual_res, c->dual_v,
                   c->hist_u[0], c->hist_u[1], c->hist_u[2], c->hist_u[3],
                   c->hist_v[0], c->hist_v[1], c->hist_v[2], c->hist_v[3],
-                  c->guess_u, c->guess_v};
+                  c->guess_u, c->guess_v, c->guess_r0, c->guess_dots};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -629,20 +629,69 @@ int fr_dual_step(fr_ctx* c, void* U, const fr_dual_opts* o, fr_dual_stats* out, 
   if (st != FR_OK) return st;
   const int order = L >= 2 ? 2 : 1;
   fr_dual_stats stats = {0, 0, NAN, NAN, extrap ? FR_GUESS_EXTRAPOLATE : FR_GUESS_PREVIOUS,
-                         {NAN, NAN}};
+                         {NAN, NAN}, 0.0, NAN};
   if (o->guess == FR_GUESS_MLP && L == 3) {
-    // the network's guess competes with the extrapolation on the residual
+    // the network's guess competes with the extrapolation on the residual,
+    // and so does the point of the segment between them where the
+    // linearised residual is least
+    const int nb = acmhd::dual_norm_blocks(c);
     if ((st = alloc_zeroed(&c->guess_u, c->bytes_state, "guess")) != FR_OK) return st;
     if ((st = alloc_zeroed((void**)&c->guess_v, nv * sizeof(double), "guess")) != FR_OK) return st;
+    if ((st = alloc_zeroed((void**)&c->guess_r0, nv * sizeof(double), "guess")) != FR_OK) return st;
+    if ((st = alloc_zeroed((void**)&c->guess_dots, (2 * (size_t)nb + 2) * sizeof(double),
+                           "guess")) != FR_OK)
+      return st;
     // the guess of this context's next level, from this context's history
     if ((st = fr_mlp_predict_for(o->mlp, c, c->guess_u, c->guess_v, stream)) != FR_OK) return st;
     st = guess_residual(c, U, c->dual_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
                         &stats.res_guess[0], s);
+    // stage 0 of the residual evaluation leaves the velocity residual in dual_vacc
+    if (st == FR_OK)
+      st = cuda_status(cudaMemcpyAsync(c->guess_r0, c->dual_vacc, nv * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s), "guess");
     if (st == FR_OK)
       st = guess_residual(c, c->guess_u, c->guess_v, c->hist_v[h0], c->hist_v[h1], o->dt, order,
                           &stats.res_guess[1], s);
+    double dots[2] = {0.0, 0.0};
+    if (st == FR_OK)
+      st = cuda_status(acmhd::launch_pair_dots(c, c->guess_r0, c->dual_vacc, c->guess_dots,
+                                               c->guess_dots + 2 * nb, s), "guess");
+    if (st == FR_OK)
+      st = cuda_status(cudaMemcpyAsync(dots, c->guess_dots + 2 * nb, sizeof(dots),
+                                       cudaMemcpyDeviceToHost, s), "guess");
+    if (st == FR_OK) st = cuda_status(cudaStreamSynchronize(s), "guess");
     if (st != FR_OK) return st;
-    if (stats.res_guess[1] < stats.res_guess[0]) {
+    // r(alpha) ~ r0 + alpha (r1 - r0): least at alpha = -<r0, r1 - r0> / |r1 - r0|^2
+    double alpha = dots[1] > 0.0 ? -dots[0] / dots[1] : 0.0;
+    alpha = std::isfinite(alpha) ? (alpha < 0.0 ? 0.0 : (alpha > 1.0 ? 1.0 : alpha)) : 0.0;
+    double best = stats.res_guess[0] <= stats.res_guess[1] ? stats.res_guess[0]
+                                                           : stats.res_guess[1];
+    double weight = stats.res_guess[1] < stats.res_guess[0] ? 1.0 : 0.0;
+    if (alpha > 0.0 && alpha < 1.0) {
+      // the blend (1 - alpha) extrapolation + alpha network, in guess_u / guess_v
+      st = cuda_status(acmhd::launch_combine3(c, c->precision, n, 1.0 - alpha, alpha, 0.0, U,
+                                              c->guess_u, nullptr, c->guess_u, s), "guess");
+      if (st == FR_OK)
+        st = cuda_status(acmhd::launch_combine3(c, FR_F64, nv, 1.0 - alpha, alpha, 0.0,
+                                                c->dual_v, c->guess_v, nullptr, c->guess_v, s),
+                         "guess");
+      double res_a = NAN;
+      if (st == FR_OK)
+        st = guess_residual(c, c->guess_u, c->guess_v, c->hist_v[h0], c->hist_v[h1], o->dt,
+                            order, &res_a, s);
+      if (st != FR_OK) return st;
+      stats.res_blend = res_a;
+      if (res_a < best) {
+        best = res_a;
+        weight = alpha;
+      } else if (weight == 1.0) {
+        // the blend lost to the network's own guess, which guess_u no longer holds
+        if ((st = fr_mlp_predict_for(o->mlp, c, c->guess_u, c->guess_v, stream)) != FR_OK)
+          return st;
+      }
+    }
+    stats.mlp_weight = weight;
+    if (weight > 0.0) {
       stats.guess_used = FR_GUESS_MLP;
       st = cuda_status(cudaMemcpyAsync(U, c->guess_u, c->bytes_state, cudaMemcpyDeviceToDevice, s),
                        "guess");

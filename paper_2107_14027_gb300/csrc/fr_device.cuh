@@ -148,7 +148,7 @@ __device__ __forceinline__ void neighbours(int e, const int* n, int (&nb)[3][2])
 //  * NW: the m^(d-1) lines of a phase come in WT = ceil(lines / (32/E))
 //    warp tasks, spread over at most 12 warps in equal rounds;
 //  * MINB: as many CTAs per SM as shared memory allows, as long as each
-//    thread keeps at least REG_FLOOR registers (the kernel is latency
+//    thread keeps at least REG_FLOOR registers (the FP32 kernel is latency
 //    bound: resident warps keep loads in flight).
 template <int D, int M, typename T>
 struct FusedCfg {
@@ -162,7 +162,11 @@ struct FusedCfg {
   static constexpr int WT = (NL + 32 / E - 1) / (32 / E);
   static constexpr int ROUNDS = (WT + 11) / 12;
   static constexpr int NW = (WT + ROUNDS - 1) / ROUNDS;
-  static constexpr int REG_FLOOR = ((M >= 6) ? 80 : 48) * int(sizeof(T) / 4);
+  // FP64 at m = 5: three CTAs per SM would cap the kernel at 80 registers
+  // and spill about 2.4 KB per thread; FP64 is bound by the FP64 pipe on
+  // GB300, so two CTAs without spills serve it better
+  static constexpr int REG_FLOOR =
+      ((M >= 6) ? 80 : (sizeof(T) == 8 && M == 5 ? 64 : 48)) * int(sizeof(T) / 4);
   static constexpr int SMEM_BLOCKS = int((228 * 1024) / (SMEM + 1024));
   static constexpr int REG_BLOCKS = 65536 / (NW * 32 * REG_FLOOR);
   static constexpr int MINB_RAW = SMEM_BLOCKS < REG_BLOCKS ? SMEM_BLOCKS : REG_BLOCKS;

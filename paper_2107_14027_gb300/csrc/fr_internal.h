@@ -123,6 +123,8 @@ struct fr_ctx {
   int hist_levels;     // number of valid levels (0..4)
   void* guess_u;       // alternative initial guess (state, precision T)
   double* guess_v;     // alternative initial guess (FP64 velocity)
+  double* guess_r0;    // pseudo residual (velocity rows, FP64) of the extrapolation
+  double* guess_dots;  // [2 dual_norm_blocks] partial sums, then the two dots
   int schedule;        // FR_SCHEDULE_* requested for the pseudo steps
 };
 
@@ -159,6 +161,10 @@ cudaError_t launch_bdf_const(const fr_ctx* c, double c1, double c2, const double
 cudaError_t launch_dual_stage(const fr_ctx* c, int stage, double dtau, double a0dt, void* U,
                               double* V, const double* C, double* partial, cudaStream_t s,
                               double dV = 1.0, double dA = 1.0);
+// out[0] = <a, b - a>, out[1] = |b - a|^2 over the real entries of two FP64
+// velocity vectors; partial holds 2 * dual_norm_blocks doubles
+cudaError_t launch_pair_dots(const fr_ctx* c, const double* a, const double* b, double* partial,
+                             double* out, cudaStream_t s);
 cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, int nparts, double count,
                               double* out, cudaStream_t s);
 cudaError_t launch_stage(const fr_ctx* c, const void* U, const void* Tr, const StageArgs& a,

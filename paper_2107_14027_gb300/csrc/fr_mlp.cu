@@ -31,6 +31,9 @@ struct fr_mlp {
   float* v[6];
   size_t cnt[6];
   int adam_t;
+  int n_val;             // the newest n_val collected samples: validation only
+  float wd;              // decoupled weight decay of Adam (weights, not biases)
+  double* val_loss;      // [1]
   float* in_scale;       // [3 nv] RMS of the feature blocks
   float* in_scale_inv;   // [3 nv]
   float* out_scale;      // [nv]
@@ -145,9 +148,10 @@ int forward(fr_mlp* q, const __nv_bfloat16* X, long long ld, int cols, float* Z1
   return st_of(acmhd::launch_gemm(acmhd::GEMM_A_NK, acmhd::GEMM_B_KM, g, s), "mlp layer 3");
 }
 
-// Loss and gradients over the collected samples (gradients into q->g).
+// Loss and gradients over the training samples, the collected ones except
+// the newest n_val (gradients into q->g).
 int loss_grad(fr_mlp* q, cudaStream_t s) {
-  const int n = q->n;
+  const int n = q->n - q->n_val;
   const long long ld = q->cap;
   int st = forward(q, q->Xs, ld, n, q->Z1, q->H1b, q->Z2, q->H2b, q->Y, nullptr, s);
   if (st != FR_OK) return st;
@@ -198,6 +202,25 @@ int loss_grad(fr_mlp* q, cudaStream_t s) {
   if ((st = st_of(acmhd::launch_gemm(acmhd::GEMM_A_NK, acmhd::GEMM_B_MK, g, s), "mlp dW1")))
     return st;
   return st_of(acmhd::launch_row_sum(q->dZ1, ld, q->H, n, q->g[1], s), "mlp db1");
+}
+
+// Loss of the current network on the validation samples (columns
+// n - n_val .. n - 1 of the sample store) into q->val_loss.
+int validation_loss(fr_mlp* q, cudaStream_t s) {
+  const int n0 = q->n - q->n_val, nv = q->n_val;
+  const long long ld = q->cap;
+  int st = forward(q, q->Xs + n0, ld, nv, q->Z1 + n0, q->H1b + n0, q->Z2 + n0, q->H2b + n0,
+                   q->Y + n0, nullptr, s);
+  if (st == FR_OK)
+    st = st_of(acmhd::launch_loss_grad(q->Y + n0, q->Ts + n0, ld, q->NO, nv, q->ctx->npts,
+                                       q->out_scale_inv, q->dY + n0, q->dYb + n0, q->partial,
+                                       q->nparts, s),
+               "mlp validation loss");
+  if (st == FR_OK)
+    st = st_of(acmhd::launch_sum_partials(q->partial, q->nparts, (double)q->NO * nv, q->val_loss,
+                                          s),
+               "mlp validation loss");
+  return st;
 }
 
 bool ptr16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -252,7 +275,8 @@ int fr_mlp_create(fr_ctx* c, int hidden, int capacity, unsigned long long seed, 
        (st = dalloc(&q->dZ1, (size_t)q->H * ld)) || (st = dalloc(&q->H1b, (size_t)q->H * ld)) ||
        (st = dalloc(&q->H2b, (size_t)q->H * ld)) || (st = dalloc(&q->dYb, (size_t)q->NO * ld)) ||
        (st = dalloc(&q->dZ2b, (size_t)q->H * ld)) || (st = dalloc(&q->dZ1b, (size_t)q->H * ld)) ||
-       (st = dalloc(&q->partial, (size_t)q->nparts)) || (st = dalloc(&q->loss, 1))))
+       (st = dalloc(&q->partial, (size_t)q->nparts)) || (st = dalloc(&q->loss, 1)) ||
+       (st = dalloc(&q->val_loss, 1))))
     ;
   if (st == FR_OK) st = st_of(cudaDeviceSynchronize(), "mlp init");
   if (st != FR_OK) {
@@ -275,7 +299,8 @@ void fr_mlp_destroy(fr_mlp* q) {
   }
   void* bufs[] = {q->in_scale, q->in_scale_inv, q->out_scale, q->out_scale_inv, q->Xs, q->Ts,
                   q->elems, q->Z1, q->Z2, q->Y, q->dY, q->dZ2, q->dZ1, q->H1b, q->H2b, q->dYb,
-                  q->dZ2b, q->dZ1b, q->partial, q->loss, q->Xi, q->Hi1, q->Hi2, q->Yc};
+                  q->dZ2b, q->dZ1b, q->partial, q->loss, q->val_loss, q->Xi, q->Hi1, q->Hi2,
+                  q->Yc};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete q;
@@ -422,8 +447,29 @@ static int set_output_scales(fr_mlp* q, cudaStream_t s) {
   return st;
 }
 
+int fr_mlp_set_training(fr_mlp* q, int n_val, double weight_decay) {
+  if (!q || n_val < 0 || n_val > q->cap || !(weight_decay >= 0.0) || !std::isfinite(weight_decay))
+    return FR_EINVAL;
+  q->n_val = n_val;
+  q->wd = static_cast<float>(weight_decay);
+  return FR_OK;
+}
+
+int fr_mlp_validation_loss(fr_mlp* q, double* loss, void* stream) {
+  if (!q || !loss || q->n_val < 1 || q->n_val >= q->n || q->adam_t == 0) return FR_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = validation_loss(q, s);
+  double l = NAN;
+  if (st == FR_OK)
+    st = st_of(cudaMemcpyAsync(&l, q->val_loss, sizeof(double), cudaMemcpyDeviceToHost, s),
+               "mlp validation loss");
+  if (st == FR_OK) st = st_of(cudaStreamSynchronize(s), "mlp validation loss");
+  *loss = l;
+  return st;
+}
+
 int fr_mlp_loss_grad(fr_mlp* q, double* loss, void* stream) {
-  if (!q || q->n < 1) return FR_EINVAL;
+  if (!q || q->n - q->n_val < 1) return FR_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int st = FR_OK;
   if (q->adam_t == 0 && (st = set_output_scales(q, s)) != FR_OK) return st;
@@ -436,7 +482,8 @@ int fr_mlp_loss_grad(fr_mlp* q, double* loss, void* stream) {
 }
 
 int fr_mlp_train(fr_mlp* q, int epochs, double lr, double* loss, void* stream) {
-  if (!q || q->n < 1 || epochs < 0 || !(lr > 0.0) || !std::isfinite(lr)) return FR_EINVAL;
+  if (!q || q->n - q->n_val < 1 || epochs < 0 || !(lr > 0.0) || !std::isfinite(lr))
+    return FR_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int st = FR_OK;
   if (q->adam_t == 0 && (st = set_output_scales(q, s)) != FR_OK) return st;
@@ -448,7 +495,8 @@ int fr_mlp_train(fr_mlp* q, int epochs, double lr, double* loss, void* stream) {
     const float c2 = 1.0f - std::pow(b2, (float)q->adam_t);
     for (int i = 0; i < 6; ++i)
       if ((st = st_of(acmhd::launch_adam(q->cnt[i], q->p[i], q->g[i], q->m[i], q->v[i], q->pb[i],
-                                         (float)lr, b1, b2, eps, c1, c2, s),
+                                         (float)lr, b1, b2, eps, c1, c2, i % 2 == 0 ? q->wd : 0.0f,
+                                         s),
                       "mlp adam")))
         return st;
   }

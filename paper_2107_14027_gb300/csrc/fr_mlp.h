@@ -66,7 +66,7 @@ cudaError_t launch_sum_partials(const double* partial, int n, double count, doub
 cudaError_t launch_row_sum(const float* dZ, long long ld, int nrows, int ncols, float* db,
                            cudaStream_t s);
 cudaError_t launch_adam(size_t n, float* p, const float* g, float* m, float* v, __nv_bfloat16* pb,
-                        float lr, float b1, float b2, float eps, float c1, float c2,
+                        float lr, float b1, float b2, float eps, float c1, float c2, float wd,
                         cudaStream_t s);
 cudaError_t launch_to_bf16(size_t n, const float* x, __nv_bfloat16* y, cudaStream_t s);
 

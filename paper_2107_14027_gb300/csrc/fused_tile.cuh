@@ -180,12 +180,26 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
                                                nb[a][1])
                           : T(0);
       }
-      // own traces, and the common fluxes at the two faces (stage 4)
+      // own traces, and the common fluxes at the two faces (stage 4).  On
+      // the y and z faces the trace kernel (or the previous fused stage)
+      // stored exactly these values (same inputs, same trace_dot); in FP64,
+      // where this kernel is bound by arithmetic on GB300, they are read
+      // back instead of recomputed (e < elem_stride: in bounds for every
+      // lane; padding lanes' values are not used)
+      constexpr bool kOwnFromMemory = sizeof(T) == 8;
       T own_lo[NS], own_hi[NS];
+      if (kOwnFromMemory && a != 0) {
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        own_lo[s] = trace_dot<M>(u[s], c.lm);
-        own_hi[s] = trace_dot<M>(u[s], c.lp);
+        for (int s = 0; s < NS; ++s) {
+          own_lo[s] = __ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S + e);
+          own_hi[s] = __ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e);
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          own_lo[s] = trace_dot<M>(u[s], c.lm);
+          own_hi[s] = trace_dot<M>(u[s], c.lp);
+        }
       }
       if (a == 0) {
 #pragma unroll

@@ -146,6 +146,40 @@ convert_kernel(size_t n, const Tin* __restrict__ x, Tout* __restrict__ y) {
     y[i] = static_cast<Tout>(x[i]);
 }
 
+// partial sums over the real entries of two FP64 velocity vectors a, b:
+// partial[2 blk] = sum a (b - a), partial[2 blk + 1] = sum (b - a)^2
+__global__ void __launch_bounds__(kThreads)
+pair_dots_kernel(size_t n, int stride, int ne, const double* __restrict__ a,
+                 const double* __restrict__ b, double* __restrict__ partial) {
+  __shared__ double red[kThreads];
+  double s0 = 0.0, s1 = 0.0;
+  for (size_t i = blockIdx.x * (size_t)kThreads + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * kThreads) {
+    if ((int)(i % (size_t)stride) >= ne) continue;
+    const double d = b[i] - a[i];
+    s0 = fma(a[i], d, s0);
+    s1 = fma(d, d, s1);
+  }
+  const double t0 = block_sum(s0, red);
+  if (threadIdx.x == 0) partial[2 * blockIdx.x] = t0;
+  __syncthreads();
+  const double t1 = block_sum(s1, red);
+  if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = t1;
+}
+
+// out[k] = sum over blocks of partial[2 blk + k], fixed order (one block)
+__global__ void __launch_bounds__(kThreads)
+pair_dots_final_kernel(int nparts, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double red[kThreads];
+  for (int k = 0; k < 2; ++k) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += kThreads) s += partial[2 * i + k];
+    const double t = block_sum(s, red);
+    if (threadIdx.x == 0) out[k] = t;
+    __syncthreads();
+  }
+}
+
 int grid_blocks(const fr_ctx* c) {
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
@@ -221,6 +255,17 @@ cudaError_t launch_dual_stage(const fr_ctx* c, int stage, double dtau, double a0
   return c->precision == FR_F32
              ? dual_stage_t<float>(c, stage, dtau, a0dt, U, V, C, partial, dV, dA, s)
              : dual_stage_t<double>(c, stage, dtau, a0dt, U, V, C, partial, dV, dA, s);
+}
+
+cudaError_t launch_pair_dots(const fr_ctx* c, const double* a, const double* b, double* partial,
+                             double* out, cudaStream_t s) {
+  const size_t n = (size_t)c->dim * c->npts * c->stride;
+  const int nb = grid_blocks(c);
+  pair_dots_kernel<<<nb, kThreads, 0, s>>>(n, (int)c->stride, c->ne, a, b, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  pair_dots_final_kernel<<<1, kThreads, 0, s>>>(nb, partial, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_norm_final(const fr_ctx* c, const double* partial, int nparts, double count,

@@ -482,7 +482,7 @@ row_sum_kernel(const float* __restrict__ dZ, long long ld, int ncols, float* __r
 __global__ void __launch_bounds__(256)
 adam_kernel(size_t n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
             float* __restrict__ v, __nv_bfloat16* __restrict__ pb, float lr, float b1, float b2,
-            float eps, float c1, float c2) {
+            float eps, float c1, float c2, float wd) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
@@ -490,7 +490,8 @@ adam_kernel(size_t n, float* __restrict__ p, const float* __restrict__ g, float*
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    // decoupled weight decay (AdamW; wd = 0: plain Adam)
+    const float pi = p[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i]);
     p[i] = pi;
     if (pb) pb[i] = __float2bfloat16(pi);
   }
@@ -628,9 +629,10 @@ cudaError_t launch_row_sum(const float* dZ, long long ld, int nrows, int ncols, 
 }
 
 cudaError_t launch_adam(size_t n, float* p, const float* g, float* m, float* v, __nv_bfloat16* pb,
-                        float lr, float b1, float b2, float eps, float c1, float c2,
+                        float lr, float b1, float b2, float eps, float c1, float c2, float wd,
                         cudaStream_t s) {
-  adam_kernel<<<blocks_for((long long)n), 256, 0, s>>>(n, p, g, m, v, pb, lr, b1, b2, eps, c1, c2);
+  adam_kernel<<<blocks_for((long long)n), 256, 0, s>>>(n, p, g, m, v, pb, lr, b1, b2, eps, c1, c2,
+                                                       wd);
   return cudaGetLastError();
 }
 

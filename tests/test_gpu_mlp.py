@@ -224,6 +224,18 @@ def test_mlp_guess_error_paths(abi):
         abi.fr_destroy(ctx)
 
 
+def _chosen_is_best(abi, s):
+    """The state iterated is the candidate (extrapolation, network, blend)
+    with the smallest initial residual, and its weight is consistent."""
+    cand = {0.0: s.res_guess[0], 1.0: s.res_guess[1]}
+    if np.isfinite(s.res_blend):
+        cand[s.mlp_weight if 0.0 < s.mlp_weight < 1.0 else -1.0] = s.res_blend
+    best = min(v for v in cand.values())
+    ok = 0.0 <= s.mlp_weight <= 1.0
+    ok &= (s.guess_used == abi.FR_GUESS_MLP) == (s.mlp_weight > 0.0)
+    return bool(ok and cand.get(s.mlp_weight, np.nan) == best)
+
+
 def test_learned_guess_gain_over_extrapolation(abi):
     """Train on samples from the first physical steps of a 2-D run, then
     compare the initial residual and the pseudo iterations to tolerance of
@@ -233,7 +245,7 @@ def test_learned_guess_gain_over_extrapolation(abi):
     U0, mesh, _, lo, hi = parity.make_case(n, order, noise=False)
     prm = fr.Params(2.5, 1.0 / 400.0, 5e-3)
     dt, dtau, tol = 1e-2, 1e-2, 1e-6
-    runs = {}
+    runs, s_m_of = {}, {}
     for mode in ("plain", "mlp"):
         ctx = abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, 64)
         net = abi.fr_mlp_create(ctx, 64, 4096, seed=11)
@@ -248,6 +260,7 @@ def test_learned_guess_gain_over_extrapolation(abi):
                 st, s = abi.fr_dual_step(ctx, Ud, dt, dtau, tol, 6000, check_every=5, guess=guess,
                                          mlp=net, allow_noconv=True)
                 res.append((s.iters, s.res, s.guess_used, tuple(s.res_guess)))
+                s_m_of[id(res[-1][3])] = s
                 if mode == "mlp" and 3 <= k < 10:
                     abi.fr_mlp_collect(net, 64, seed=100 + k)
                 if mode == "mlp" and k == 9:
@@ -261,8 +274,8 @@ def test_learned_guess_gain_over_extrapolation(abi):
     chosen = 0
     for (it_p, r_p, _, _), (it_m, r_m, used, rg) in zip(runs["plain"][10:], runs["mlp"][10:]):
         assert r_m < tol and r_p < tol
-        # the learned step starts from the better of the two guesses
-        assert min(rg) == (rg[1] if used == abi.FR_GUESS_MLP else rg[0])
+        # the learned step starts from the best of the candidates
+        assert _chosen_is_best(abi, s_m_of[id(rg)])
         chosen += used == abi.FR_GUESS_MLP
     # the trained network beats the extrapolation on some held-out step, and
     # the learned run needs fewer pseudo iterations in total
@@ -344,8 +357,7 @@ def test_learned_guess_gain_in_3d_through_a_fork(abi):
             _, sb = abi.fr_dual_step(B, Ub, dt, dtau, tol, 6000, check_every=5,
                                      guess=abi.FR_GUESS_MLP, mlp=net)
             assert sa.res < tol and sb.res < tol
-            assert min(sb.res_guess) == (sb.res_guess[1] if sb.guess_used == abi.FR_GUESS_MLP
-                                         else sb.res_guess[0])
+            assert _chosen_is_best(abi, sb)
             chosen += sb.guess_used == abi.FR_GUESS_MLP
             plain.append(sa.iters)
             learned.append(sb.iters)
@@ -405,4 +417,46 @@ def test_save_load_round_trip(abi, tmp_path):
         if net2:
             abi.fr_mlp_destroy(net2)
         abi.fr_destroy(other)
+        abi.fr_destroy(ctx)
+
+
+def test_validation_split_and_weight_decay_match_oracle(abi):
+    """With the newest 10 of 40 samples held out and weight decay 0.3: the
+    training loss is the oracle's on the other 30, one Adam step is the
+    oracle's AdamW step from the GPU gradients, and the validation loss is
+    the oracle's on the held-out 10 with the new weights."""
+    ctx, Ud, levels, nv = _history_case(abi)
+    H, S, NVAL, WD = 32, 40, 10, 0.3
+    net = abi.fr_mlp_create(ctx, H, S, seed=9)
+    try:
+        K, _, NO, _, npar = abi.fr_mlp_info(net)
+        el = abi.fr_mlp_collect(net, S, seed=5)
+        abi.fr_mlp_set_training(net, NVAL, WD)
+        loss = abi.fr_mlp_loss_grad(net)
+        scales = abi.fr_mlp_params(net, 2, count=4 * nv)
+        t = scales[3 * nv:].astype(np.float64)
+        sizes = [(H, K), (H, H), (NO, H)]
+        params = _unflatten(abi.fr_mlp_params(net, 0, count=npar), sizes)
+        grads = _unflatten(abi.fr_mlp_params(net, 1, count=npar), sizes)
+        X = abi.fr_mlp_params(net, 3, count=K * S).reshape(K, S).astype(np.float64)
+        Un, Unm1, Unm2, Unp1 = levels[-2], levels[-3], levels[-4], levels[-1]
+        Tg = omlp.targets(Unp1, Un, Unm1, Unm2, t, el)
+        ntr = S - NVAL
+        Y, _ = omlp.forward(params, X[:, :ntr])
+        lo = omlp.loss(Y, Tg[:, :ntr])
+        assert abs(loss - lo) <= BF16_TOL * lo, (loss, lo)
+        abi.fr_mlp_train(net, 1, 1e-3)
+        new = _unflatten(abi.fr_mlp_params(net, 0, count=npar), sizes)
+        expect = omlp.Adam(params, lr=1e-3, weight_decay=WD).step(params, grads)
+        for (W0, b0), (W1, b1), (E1, e1) in zip(params, new, expect):
+            for p0, p1, pe in ((W0, W1, E1), (b0, b1, e1)):
+                np.testing.assert_allclose(p0 - p1, p0 - pe, rtol=1e-4, atol=1e-7)
+        vl = abi.fr_mlp_validation_loss(net)
+        Yv, _ = omlp.forward(new, X[:, ntr:])
+        lv = omlp.loss(Yv, Tg[:, ntr:])
+        assert abs(vl - lv) <= BF16_TOL * lv, (vl, lv)
+        with pytest.raises(abi.FrError):
+            abi.fr_mlp_set_training(net, -1, 0.0)
+    finally:
+        abi.fr_mlp_destroy(net)
         abi.fr_destroy(ctx)

@@ -88,3 +88,35 @@ def test_extrapolation_targets_vanish_for_quadratic_histories():
     np.testing.assert_allclose(X[14 * 9:, 0], (2.0 * c / 0.5)[:, :, 1].reshape(-1), atol=1e-12)
     G = mlp.apply_guess(np.zeros((7 * 9, 4)), U[2], U[1], U[0], np.ones(7))
     np.testing.assert_allclose(G, U[3], atol=1e-12)
+
+
+def test_adamw_decay_with_zero_gradient():
+    """With a zero gradient Adam's moments stay zero, so the step is the pure
+    decoupled decay: W <- (1 - lr wd) W, biases unchanged."""
+    import numpy as np
+    from oracle import mlp as omlp
+    rng = np.random.default_rng(0)
+    params = [(rng.normal(size=(4, 3)), rng.normal(size=4)), (rng.normal(size=(2, 4)),
+                                                              rng.normal(size=2))]
+    zeros = [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
+    opt = omlp.Adam(params, lr=1e-2, weight_decay=0.5)
+    new = opt.step(params, zeros)
+    for (W, b), (W1, b1) in zip(params, new):
+        np.testing.assert_allclose(W1, (1 - 1e-2 * 0.5) * W, rtol=1e-15)
+        np.testing.assert_array_equal(b1, b)
+
+
+def test_blend_weight_minimises_a_linear_residual_on_the_segment():
+    import numpy as np
+    from oracle import mlp as omlp
+    rng = np.random.default_rng(2)
+    A = rng.normal(size=(30, 12))
+    f = rng.normal(size=30)
+    for trial in range(20):
+        u0, u1 = rng.normal(size=12), rng.normal(size=12)
+        r0, r1 = A @ u0 - f, A @ u1 - f
+        alpha = omlp.blend_weight(r0, r1)
+        grid = np.linspace(0.0, 1.0, 20001)
+        res = [np.linalg.norm(A @ ((1 - a) * u0 + a * u1) - f) for a in grid]
+        best = grid[int(np.argmin(res))]
+        assert abs(alpha - best) <= 1e-4, (alpha, best)
