@@ -459,6 +459,14 @@ def run_gpu(args):
     t64_fused = _time_loop(lambda: abi.fr_rhs_volume(ctx64, Ud64, Rd64, stream), stream,
                            max(K // 2, 5), 2, torch) / max(K // 2, 5)
     abi.fr_destroy(ctx64)
+    # the same RHS in the double-float mode (FP64 storage, ~48-bit arithmetic)
+    ctxdf = abi.fr_create(n, cfg["lo"], cfg["hi"], order, nv, cfg["zeta"], cfg["nu"], cfg["t_r"],
+                          abi.FR_DF64, abi.FR_CORR_DG)
+    tdf = _time_loop(lambda: abi.fr_rhs(ctxdf, Ud64, Rd64, stream), stream, max(K // 2, 5), 2,
+                     torch) / max(K // 2, 5)
+    tdf_fused = _time_loop(lambda: abi.fr_rhs_volume(ctxdf, Ud64, Rd64, stream), stream,
+                           max(K // 2, 5), 2, torch) / max(K // 2, 5)
+    abi.fr_destroy(ctxdf)
     del Ud64, Rd64
     torch.cuda.empty_cache()
     # FMA peaks of this GPU (probe kernel), FP64 and FP32
@@ -515,6 +523,9 @@ def run_gpu(args):
                         "fused_speedup": t_unf / t_rhs_only},
             "fp64": {"value": dof / t64 / 1e9, "ms": 1e3 * t64, "fused_ms": 1e3 * t64_fused,
                      "roofline": fp64_roofline},
+            "df64": {"value": dof / tdf / 1e9, "ms": 1e3 * tdf, "fused_ms": 1e3 * tdf_fused,
+                     "speedup_over_fp64": t64 / tdf,
+                     "arithmetic": "double-float (two FP32, ~48 bits), FP64 storage"},
             "fma_peak_tflops": {"fp64": probe[abi.FR_F64] / 1e12,
                                 "fp32": probe[abi.FR_F32] / 1e12},
             "gpu_launches": 2 * args.steps,
@@ -565,7 +576,8 @@ class _DualSolver:
         zeta, nu, t_r = 2.5, 1.0 / 1600.0, 5e-3
         self.refine = prec == abi.FR_F32 and args.dual_tol < _TOL_SWITCH
         self.c = abi.fr_create(n, lo, hi, order, 13, zeta, nu, t_r, prec)
-        self.c64 = abi.fr_create(n, lo, hi, order, 13, zeta, nu, t_r, abi.FR_F64) if self.refine \
+        twin = abi.FR_DF64 if args.dual_twin == "df64" else abi.FR_F64
+        self.c64 = abi.fr_create(n, lo, hi, order, 13, zeta, nu, t_r, twin) if self.refine \
             else None
         self.U = abi.pack_state(self.c, U0, prec)
         self.U64 = abi.new_state(self.c64, abi.FR_F64) if self.refine else None
@@ -626,6 +638,7 @@ def _dual_config(args, workload, extra):
                       "pmg-aa": "P-multigrid cycles p..1, Anderson mixing in the FP64 phase "
                                 "(iters = cycles)"}[args.dual_solver],
            "anderson": args.dual_anderson if args.dual_solver == "pmg-aa" else 0,
+           "fp64_twin": args.dual_twin,
            "pmg_factors": args.dual_pmg_factors or "1.75^(p-q)"}
     cfg.update(extra)
     return cfg
@@ -634,7 +647,8 @@ def _dual_config(args, workload, extra):
 def _rec(k, st, s, wall):
     return {"step": k, "wall_s": wall, "iters": s.iters, "iters_fp64": s.iters_refine,
             "res": s.res, "res_switch": s.res_switch, "guess": s.guess_used,
-            "res_guess": list(s.res_guess), "converged": st == 0}
+            "res_guess": list(s.res_guess), "mlp_weight": s.mlp_weight,
+            "res_blend": s.res_blend, "converged": st == 0}
 
 
 def run_dual(args):
@@ -991,6 +1005,9 @@ def main():
     ap.add_argument("--dual-solver", default="pmg-aa", choices=["rk4", "pmg", "pmg-aa"],
                     help="pseudo solver: RK4 steps, P-multigrid cycles, or cycles with "
                          "Anderson mixing in the FP64 phase (default)")
+    ap.add_argument("--dual-twin", default="df64", choices=["df64", "f64"],
+                    help="arithmetic of the FP64 twin below the FP32 floor: double-float "
+                         "(FP64 storage, ~48-bit arithmetic on the FP32 pipes) or FP64")
     ap.add_argument("--dual-pmg-factors", default="",
                     help="pseudo-step multipliers for orders p, p-1, .., 1 (default 1.75^(p-q))")
     ap.add_argument("--dual-anderson", type=int, default=8, help="Anderson memory (pmg-aa)")

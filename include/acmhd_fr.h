@@ -72,7 +72,13 @@ enum {
     FR_ENOMEM = -5       /* device or host allocation failed */
 };
 
-enum { FR_F32 = 32, FR_F64 = 64 };           /* arithmetic precision */
+/* arithmetic precision.  FR_DF64: states stored in FP64 (exactly as FR_F64),
+ * the trace and volume kernels computing in double-float arithmetic - each
+ * value an unevaluated sum of two FP32 numbers, about 48 significant bits
+ * (relative rounding about 3.6e-15) in FP32's exponent range - which runs on
+ * the FP32 pipes, 74 times faster than GB300's FP64 pipe; the update,
+ * residual and BDF kernels stay FP64.  Contexts report FR_F64 storage. */
+enum { FR_F32 = 32, FR_F64 = 64, FR_DF64 = 65 };
 enum { FR_GUESS_PREVIOUS = 0, FR_GUESS_EXTRAPOLATE = 1, FR_GUESS_MLP = 2 };  /* fr_dual_step guess */
 
 typedef struct fr_mlp fr_mlp;
@@ -89,7 +95,7 @@ enum {
  *   zeta        artificial compressibility zeta > 0 (Sec. 2.2)
  *   nu          kinematic viscosity nu >= 0
  *   t_r         relaxation time T_r > 0 of the auxiliary equations
- *   precision   FR_F32 or FR_F64
+ *   precision   FR_F32, FR_F64 or FR_DF64
  *   correction  FR_CORR_DG (right Radau, h_l = R_{R,p+1}) or FR_CORR_G2 (Huynh)
  * Allocates the context's device scratch on the current device.
  * Returns FR_EINVAL for bad arguments, FR_ENOMEM/FR_ECUDA on allocation

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libacmhd_fr.so")
 
 FR_OK, FR_EINVAL, FR_ECUDA, FR_ENOCONV, FR_ENONFINITE, FR_ENOMEM = 0, -1, -2, -3, -4, -5
-FR_F32, FR_F64 = 32, 64
+FR_F32, FR_F64, FR_DF64 = 32, 64, 65
 FR_CORR_DG, FR_CORR_G2 = 0, 1
 FR_GUESS_PREVIOUS, FR_GUESS_EXTRAPOLATE, FR_GUESS_MLP = 0, 1, 2
 FR_SCHEDULE_AUTO, FR_SCHEDULE_TWO_KERNELS, FR_SCHEDULE_FUSED_STAGE = 0, 1, 3

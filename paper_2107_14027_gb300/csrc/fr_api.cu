@@ -197,6 +197,7 @@ int rhs_host_pipelined(fr_ctx* c, const void* U_host, void* R_host, const int* b
 // traffic as fast as the separate update kernel does.  FP64 (ALU bound on
 // this part): equal times at p = 1..3.
 bool use_fused_stage(const fr_ctx* c) {
+  if (c->df64) return false;   // the fused stage has no double-float instance
   return c->schedule == FR_SCHEDULE_FUSED_STAGE ||
          (c->schedule == FR_SCHEDULE_AUTO && c->order <= 3);
 }
@@ -265,6 +266,7 @@ int acmhd::status_of(cudaError_t e, const char* where) { return cuda_status(e, w
 
 void acmhd::fill_const(const fr_ctx* c, FrConst<float>* k) { fill_const_t(c, k); }
 void acmhd::fill_const(const fr_ctx* c, FrConst<double>* k) { fill_const_t(c, k); }
+void acmhd::fill_const(const fr_ctx* c, FrConst<df64>* k) { fill_const_t(c, k); }
 
 void acmhd::set_last_error(const char* msg) {
   std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
@@ -280,7 +282,7 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
   if (d != 2 && d != 3) return FR_EINVAL;
   if (order < 1 || order > acmhd::kMaxM - 1) return FR_EINVAL;
   if (nvars != 1 + d + d * d) return FR_EINVAL;
-  if (precision != FR_F32 && precision != FR_F64) return FR_EINVAL;
+  if (precision != FR_F32 && precision != FR_F64 && precision != FR_DF64) return FR_EINVAL;
   if (correction != FR_CORR_DG && correction != FR_CORR_G2) return FR_EINVAL;
   if (!(zeta > 0.0) || !(nu >= 0.0) || !(t_r > 0.0) || !std::isfinite(zeta) ||
       !std::isfinite(nu) || !std::isfinite(t_r))
@@ -301,7 +303,10 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
   c->order = order;
   c->m = order + 1;
   c->nv = nvars;
-  c->precision = precision;
+  // FR_DF64 stores FP64 like FR_F64 (every buffer and the FP64 kernels treat
+  // it so); only the trace and volume kernels compute in double-float
+  c->precision = precision == FR_DF64 ? FR_F64 : precision;
+  c->df64 = precision == FR_DF64 ? 1 : 0;
   c->correction = correction;
   c->mesh = *mesh;
   c->zeta = zeta;
@@ -311,7 +316,7 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
   c->stride = (static_cast<size_t>(ne) + 31) / 32 * 32;
   c->npts = 1;
   for (int a = 0; a < d; ++a) c->npts *= c->m;
-  c->elem_bytes = precision == FR_F32 ? 4 : 8;
+  c->elem_bytes = c->precision == FR_F32 ? 4 : 8;
   c->bytes_state = (size_t)c->nv * c->npts * c->stride * c->elem_bytes;
   if (c->stride > 0x7fffffff) {
     delete c;
@@ -323,6 +328,7 @@ int fr_create(const fr_mesh* mesh, int order, int nvars, double zeta, double nu,
   }
   acmhd::fill_const(c, &c->cf);
   acmhd::fill_const(c, &c->cd);
+  acmhd::fill_const(c, &c->cdf);
 
   int st = cuda_status(cudaGetDevice(&c->device), "cudaGetDevice");
   if (st == FR_OK) {

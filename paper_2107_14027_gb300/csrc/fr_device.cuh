@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
 #include "fr_internal.h"
 #include "per_device_once.h"
 
@@ -33,6 +34,17 @@ __device__ __forceinline__ float vabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double vabs(double a) { return fabs(a); }
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+// double-float versions (df64.cuh; every operation is already exactly rounded
+// in a fixed order)
+__device__ __forceinline__ df64 rn_mul(df64 a, df64 b) { return df_mul(a, b); }
+__device__ __forceinline__ df64 rn_add(df64 a, df64 b) { return df_add(a, b); }
+__device__ __forceinline__ df64 rn_sub(df64 a, df64 b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df64 rn_fma(df64 a, df64 b, df64 c) { return df_add(df_mul(a, b), c); }
+__device__ __forceinline__ df64 rn_sqrt(df64 a) { return df_sqrt(a); }
+__device__ __forceinline__ df64 vabs(df64 a) { return a.hi < 0.0f ? df_neg(a) : a; }
+__device__ __forceinline__ df64 vmax(df64 a, df64 b) {
+  return (a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo)) ? a : b;
+}
 
 // variable index of d(V_i)/dx_b
 template <int D>

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "acmhd_fr.h"
+#include "df64.cuh"
 
 namespace acmhd {
 
@@ -92,6 +93,8 @@ struct fr_ctx {
   acmhd::Ops1D ops;
   acmhd::FrConst<float> cf;
   acmhd::FrConst<double> cd;
+  acmhd::FrConst<acmhd::df64> cdf;
+  int df64;            // FR_DF64: FP64 storage, double-float arithmetic in the RHS kernels
   // device scratch owned by the context
   void* trace;         // [2d faces][1+2d slots][m^(d-1)][stride]
   size_t trace_bytes;
@@ -135,6 +138,7 @@ namespace acmhd {
 // by fr_create and fr_rhs_static alike).
 void fill_const(const fr_ctx* c, FrConst<float>* k);
 void fill_const(const fr_ctx* c, FrConst<double>* k);
+void fill_const(const fr_ctx* c, FrConst<df64>* k);
 
 // Allocate (on first use) a context's RK4 registers / FP64 dual-time
 // registers; map a CUDA status to an FR_* code (recording its text).

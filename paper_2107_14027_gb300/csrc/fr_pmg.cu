@@ -111,8 +111,8 @@ int fr_pmg_create(fr_ctx* c, int coarsest_order, fr_pmg** out) {
   for (int q = 0; q <= p; ++q) m->factor[q] = std::pow(1.75, p - q);
   int st = FR_OK;
   for (int q = m->pmin; q < p && st == FR_OK; ++q) {
-    st = fr_create(&c->mesh, q, c->nv, c->zeta, c->nu, c->t_r, c->precision, c->correction,
-                   &m->lev[q]);
+    st = fr_create(&c->mesh, q, c->nv, c->zeta, c->nu, c->t_r, c->df64 ? FR_DF64 : c->precision,
+                   c->correction, &m->lev[q]);
     if (st == FR_OK) st = acmhd::ensure_rk_registers(m->lev[q]);
     const size_t b = st == FR_OK ? m->lev[q]->bytes_state : 0;
     if (st == FR_OK) st = alloc(&m->U[q], b);

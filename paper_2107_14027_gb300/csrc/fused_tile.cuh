@@ -17,15 +17,16 @@ namespace acmhd {
 // out.load_in), so that the stores, which the compiler must assume may alias
 // later loads, do not serialise the loads behind them.
 //
-// RhsOut stores R, from the thread that finishes the entry.
-template <typename T>
+// RhsOut stores R (storage type S, computed in T), from the thread that
+// finishes the entry.
+template <typename T, typename S = T>
 struct RhsOut {
   static constexpr bool kStage = false;
   struct Pre {};
-  T* __restrict__ R;
+  S* __restrict__ R;
   __device__ __forceinline__ Pre load_in(size_t, T) const { return Pre{}; }
   __device__ __forceinline__ T store(size_t i, T r, const Pre&) {
-    R[i] = r;
+    R[i] = cvt<S>(r);
     return r;
   }
 };
@@ -116,6 +117,8 @@ struct StageOut {
 };
 
 // Stages 2-6 for one tile of E elements starting at e0 (a multiple of E).
+// U, Tr hold values of the storage type S; the arithmetic runs in T (S = T,
+// or S = double with T = df64, the double-float mode).
 // sU, sA: shared memory of (1+D) NP E values each.  Every thread of the CTA
 // must call it (it synchronises the CTA).
 // RhsOut: each entry is stored by the thread that finishes it.
@@ -127,8 +130,8 @@ struct StageOut {
 // entries, and their traces on all faces are taken from sA.  Traces go to
 // out.tr (layout of the trace kernel, x faces only where the lane exchange
 // cannot serve them).
-template <int D, int M, typename T, int E, int NW, class Out>
-__device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __restrict__ Tr,
+template <int D, int M, typename T, int E, int NW, class Out, typename S>
+__device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __restrict__ Tr,
                                            Out& out, const FrConst<T>& c, int e0, T* sU,
                                            T* sA) {
   constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
@@ -136,12 +139,12 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
   const int el = lane % E, sub = lane / E;
   const int e = e0 + el;
   const bool valid = e < c.ne;
-  const size_t S = c.stride;
+  const size_t Sd = c.stride;
 
   // stage P and V of the tile (rows of E contiguous values)
   for (int idx = tid; idx < (1 + D) * NP * E; idx += NW * 32) {
     const int row = idx / E, x = idx - row * E;
-    sU[idx] = __ldg(U + (size_t)row * S + e0 + x);
+    sU[idx] = cvt<T>(__ldg(U + (size_t)row * Sd + e0 + x));
   }
   int nb[3][2];
   neighbours<D>(valid ? e : 0, c.n, nb);
@@ -163,7 +166,7 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
         for (int s = 0; s <= D; ++s) u[s][t] = sU[(s * NP + pt) * E + el];
 #pragma unroll
         for (int i = 0; i < D; ++i)
-          u[1 + D + i][t] = __ldg(U + ((size_t)aux_var<D>(i, a) * NP + pt) * S + e);
+          u[1 + D + i][t] = cvt<T>(__ldg(U + ((size_t)aux_var<D>(i, a) * NP + pt) * Sd + e));
       }
       // neighbour traces: issued right after the line's own loads.  In the
       // x phase a neighbour inside the lane group is served by a shuffle
@@ -173,11 +176,11 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
       T nb_lo[NS], nb_hi[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        nb_lo[s] = lo_mem ? __ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S +
-                                               nb[a][0])
+        nb_lo[s] = lo_mem ? cvt<T>(__ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd +
+                                          nb[a][0]))
                           : T(0);
-        nb_hi[s] = hi_mem ? __ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S +
-                                               nb[a][1])
+        nb_hi[s] = hi_mem ? cvt<T>(__ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * Sd +
+                                          nb[a][1]))
                           : T(0);
       }
       // own traces, and the common fluxes at the two faces (stage 4).  On
@@ -191,21 +194,23 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
       if (kOwnFromMemory && a != 0) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-          own_lo[s] = __ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * S + e);
-          own_hi[s] = __ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e);
+          own_lo[s] = cvt<T>(__ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * Sd + e));
+          own_hi[s] = cvt<T>(__ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + e));
         }
       } else {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-          own_lo[s] = trace_dot<M>(u[s], c.lm);
-          own_hi[s] = trace_dot<M>(u[s], c.lp);
+          // through the storage type, as the trace kernel stores them, so
+          // both elements of a face use identical values
+          own_lo[s] = cvt<T>(cvt<S>(trace_dot<M>(u[s], c.lm)));
+          own_hi[s] = cvt<T>(cvt<S>(trace_dot<M>(u[s], c.lp)));
         }
       }
       if (a == 0) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-          const T from_left = __shfl_up_sync(0xffffffffu, own_hi[s], 1, E);
-          const T from_right = __shfl_down_sync(0xffffffffu, own_lo[s], 1, E);
+          const T from_left = shfl_up(own_hi[s], 1, E);
+          const T from_right = shfl_down(own_lo[s], 1, E);
           if (!lo_mem) nb_lo[s] = from_left;
           if (!hi_mem) nb_hi[s] = from_right;
         }
@@ -224,7 +229,7 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
 #pragma unroll
           for (int t = 0; t < M; ++t)
             pq[t] = out.load_in(((size_t)aux_var<D>(s - D - 1, a) * NP + line_pt<D, M>(a, l, t)) *
-                                    S + e,
+                                    Sd + e,
                                 u[s][t]);
         }
         T f[M];
@@ -248,12 +253,12 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
             } else if (a < D - 1 || Out::kStage) {
               sA[idx] += r;
             } else {
-              out.store(((size_t)s * NP + pt) * S + e, sA[idx] + r, typename Out::Pre{});
+              out.store(((size_t)s * NP + pt) * Sd + e, sA[idx] + r, typename Out::Pre{});
             }
           } else {
             // auxiliary equation of slot s: finished here, with its source
             const int v = aux_var<D>(s - D - 1, a);
-            nx = out.store(((size_t)v * NP + pt) * S + e, fma(-u[s][i], c.inv_t, r),
+            nx = out.store(((size_t)v * NP + pt) * Sd + e, fma(-u[s][i], c.inv_t, r),
                            pq[i]);
           }
           if constexpr (Out::kStage) {
@@ -264,8 +269,8 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
         if constexpr (Out::kStage) {
           const bool w_lo = (a != 0) || !x_pair_on_chip(nb[0][0], e, E);
           const bool w_hi = (a != 0) || !x_pair_on_chip(e, nb[0][1], E);
-          if (s > D && w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * S + e] = t_lo;
-          if (s > D && w_hi) out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e] = t_hi;
+          if (s > D && w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + e] = t_lo;
+          if (s > D && w_hi) out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + e] = t_hi;
         }
       }
     }
@@ -278,7 +283,7 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
     constexpr int NPE = NP * E, TOT = (1 + D) * NPE, NT = NW * 32;
     auto gidx = [&](int idx) {
       const int row = idx / E;
-      return (size_t)row * S + e0 + (idx - row * E);
+      return (size_t)row * Sd + e0 + (idx - row * E);
     };
     auto real = [&](int idx, int end) { return idx < end && e0 + idx % E < c.ne; };
     // plain rows: P, and V unless `dual`; KB entries per thread in flight
@@ -325,9 +330,9 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
           T x[M];
 #pragma unroll
           for (int t = 0; t < M; ++t) x[t] = sA[(s * NP + line_pt<D, M>(a, l, t)) * E + el];
-          if (w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * S + e] = trace_dot<M>(x, c.lm);
+          if (w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + e] = trace_dot<M>(x, c.lm);
           if (w_hi)
-            out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e] = trace_dot<M>(x, c.lp);
+            out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + e] = trace_dot<M>(x, c.lp);
         }
       }
     }
@@ -338,33 +343,33 @@ __device__ __forceinline__ void fused_tile(const T* __restrict__ U, const T* __r
 // start at tile tile0 (the host-buffer pipeline runs the mesh in slabs);
 // the whole-mesh kernel keeps the tile index free of the offset (measured:
 // the offset alone cost 2 % of the 64^3 p=3 volume kernel's time).
-template <int D, int M, typename T, int E, int NW, int MINB, bool RANGED>
+template <int D, int M, typename S, typename T, int E, int NW, int MINB, bool RANGED>
 __global__ void __launch_bounds__(NW * 32, MINB)
-fused_kernel(const T* __restrict__ U, const T* __restrict__ Tr, T* __restrict__ R,
+fused_kernel(const S* __restrict__ U, const S* __restrict__ Tr, S* __restrict__ R,
              const FrConst<T> c, int tile0) {
   constexpr int NP = ipow<M>(D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sU = reinterpret_cast<T*>(smem_raw);  // [1+D][NP][E]
   T* sA = sU + (1 + D) * NP * E;           // [1+D][NP][E]
-  RhsOut<T> out{R};
+  RhsOut<T, S> out{R};
   const int tile = RANGED ? tile0 + (int)blockIdx.x : (int)blockIdx.x;
   fused_tile<D, M, T, E, NW>(U, Tr, out, c, tile * E, sU, sA);
 }
 
 // elements [e_begin, e_end); e_begin a multiple of 32 (and so of E), and 0
 // unless RANGED
-template <int D, int M, typename T, bool RANGED>
+template <int D, int M, typename S, typename T, bool RANGED>
 cudaError_t fused_launch(const FrConst<T>& c, const void* U, const void* Tr, void* R, int e_begin,
                          int e_end, cudaStream_t s) {
   using C = FusedCfg<D, M, T>;
-  auto kern = fused_kernel<D, M, T, C::E, C::NW, C::MINB, RANGED>;
+  auto kern = fused_kernel<D, M, S, T, C::E, C::NW, C::MINB, RANGED>;
   static PerDeviceOnce smem_once;  // per template instance
   cudaError_t err = set_smem_limit(smem_once, kern, C::SMEM);
   if (err != cudaSuccess) return err;
   const int nblk = (e_end - e_begin + C::E - 1) / C::E;
   if (nblk <= 0) return cudaSuccess;
-  kern<<<nblk, C::NW * 32, C::SMEM, s>>>(static_cast<const T*>(U), static_cast<const T*>(Tr),
-                                          static_cast<T*>(R), c, e_begin / C::E);
+  kern<<<nblk, C::NW * 32, C::SMEM, s>>>(static_cast<const S*>(U), static_cast<const S*>(Tr),
+                                          static_cast<S*>(R), c, e_begin / C::E);
   return cudaGetLastError();
 }
 

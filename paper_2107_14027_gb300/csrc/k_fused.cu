@@ -33,10 +33,16 @@ namespace acmhd {
 cudaError_t launch_fused(const fr_ctx* c, const void* U, const void* Tr, void* R, cudaStream_t s) {
   if (c->precision == FR_F32) {
     ACMHD_DISPATCH_DM(c->dim, c->m,
-                      return (fused_launch<D_, M_, float, false>(c->cf, U, Tr, R, 0, c->ne, s)));
+                      return (fused_launch<D_, M_, float, float, false>(c->cf, U, Tr, R, 0, c->ne,
+                                                                       s)));
+  } else if (c->df64) {
+    ACMHD_DISPATCH_DM(c->dim, c->m,
+                      return (fused_launch<D_, M_, double, df64, false>(c->cdf, U, Tr, R, 0, c->ne,
+                                                                       s)));
   } else {
     ACMHD_DISPATCH_DM(c->dim, c->m,
-                      return (fused_launch<D_, M_, double, false>(c->cd, U, Tr, R, 0, c->ne, s)));
+                      return (fused_launch<D_, M_, double, double, false>(c->cd, U, Tr, R, 0,
+                                                                         c->ne, s)));
   }
   return cudaErrorInvalidValue;
 }

@@ -11,11 +11,15 @@ cudaError_t launch_fused_range(const fr_ctx* c, const void* U, const void* Tr, v
   if (c->precision == FR_F32) {
     ACMHD_DISPATCH_DM(
         c->dim, c->m,
-        return (fused_launch<D_, M_, float, true>(c->cf, U, Tr, R, e_begin, e_end, s)));
+        return (fused_launch<D_, M_, float, float, true>(c->cf, U, Tr, R, e_begin, e_end, s)));
+  } else if (c->df64) {
+    ACMHD_DISPATCH_DM(
+        c->dim, c->m,
+        return (fused_launch<D_, M_, double, df64, true>(c->cdf, U, Tr, R, e_begin, e_end, s)));
   } else {
     ACMHD_DISPATCH_DM(
         c->dim, c->m,
-        return (fused_launch<D_, M_, double, true>(c->cd, U, Tr, R, e_begin, e_end, s)));
+        return (fused_launch<D_, M_, double, double, true>(c->cd, U, Tr, R, e_begin, e_end, s)));
   }
   return cudaErrorInvalidValue;
 }

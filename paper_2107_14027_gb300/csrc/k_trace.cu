@@ -22,9 +22,11 @@ constexpr bool trace_stages_pv() {
   return size_t(1 + D) * ipow<M>(D) * 32 * sizeof(T) <= 32 * 1024;
 }
 
-template <int D, int M, typename T, int E, int EF>
+// U, Tr hold the storage type S; the interpolation runs in T (S = T, or
+// S = double with T = df64), and the stored trace is its value in S.
+template <int D, int M, typename S, typename T, int E, int EF>
 __global__ void __launch_bounds__(256)
-trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c, int tile0) {
+trace_kernel(const S* __restrict__ U, S* __restrict__ Tr, const FrConst<T> c, int tile0) {
   constexpr int NP = ipow<M>(D), NL = ipow<M>(D - 1), NS = 1 + 2 * D, SUB = 32 / E;
   constexpr bool PV = trace_stages_pv<D, M, T>();
   __shared__ T sPV[PV ? (1 + D) * NP * E : 1];
@@ -37,12 +39,12 @@ trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c, in
     // rows of E contiguous elements; the tile lies inside the padded stride
     for (int idx = threadIdx.x; idx < (1 + D) * NP * E; idx += blockDim.x) {
       const int row = idx / E, x = idx - row * E;
-      sPV[idx] = __ldg(U + (size_t)row * c.stride + tile * E + x);
+      sPV[idx] = cvt<T>(__ldg(U + (size_t)row * c.stride + tile * E + x));
     }
     __syncthreads();
   }
   if (e >= c.ne) return;
-  const size_t S = c.stride;
+  const size_t Sd = c.stride;
   int nb[3][2];
   neighbours<D>(e, c.n, nb);
   // x faces: stored only where the fused kernel (EF elements per lane
@@ -64,28 +66,29 @@ trace_kernel(const T* __restrict__ U, T* __restrict__ Tr, const FrConst<T> c, in
         for (int t = 0; t < M; ++t) {
           const int pt = line_pt<D, M>(a, l, t);
           x[s][t] = (PV && s <= D) ? sPV[(s * NP + pt) * E + el]
-                                   : __ldg(U + ((size_t)v * NP + pt) * S + e);
+                                   : cvt<T>(__ldg(U + ((size_t)v * NP + pt) * Sd + e));
         }
       }
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        if (need_lo) Tr[(((size_t)(2 * a) * NS + s) * NL + l) * S + e] = trace_dot<M>(x[s], c.lm);
+        if (need_lo)
+          Tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + e] = cvt<S>(trace_dot<M>(x[s], c.lm));
         if (need_hi)
-          Tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * S + e] = trace_dot<M>(x[s], c.lp);
+          Tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + e] = cvt<S>(trace_dot<M>(x[s], c.lp));
       }
     }
   }
 }
 
 // elements [e_begin, e_end); e_begin a multiple of 32
-template <int D, int M, typename T>
+template <int D, int M, typename S, typename T>
 cudaError_t trace_launch(const FrConst<T>& c, const void* U, void* Tr, int e_begin, int e_end,
                          cudaStream_t s) {
   constexpr int E = 32;
   const int nblk = (e_end - e_begin + E - 1) / E;
   if (nblk <= 0) return cudaSuccess;
-  trace_kernel<D, M, T, E, FusedCfg<D, M, T>::E>
-      <<<nblk, 256, 0, s>>>(static_cast<const T*>(U), static_cast<T*>(Tr), c, e_begin / E);
+  trace_kernel<D, M, S, T, E, FusedCfg<D, M, T>::E>
+      <<<nblk, 256, 0, s>>>(static_cast<const S*>(U), static_cast<S*>(Tr), c, e_begin / E);
   return cudaGetLastError();
 }
 
@@ -94,10 +97,14 @@ cudaError_t launch_trace_range(const fr_ctx* c, const void* U, void* Tr, int e_b
   if (e_begin % 32 != 0) return cudaErrorInvalidValue;
   if (c->precision == FR_F32) {
     ACMHD_DISPATCH_DM(c->dim, c->m,
-                      return (trace_launch<D_, M_, float>(c->cf, U, Tr, e_begin, e_end, s)));
+                      return (trace_launch<D_, M_, float, float>(c->cf, U, Tr, e_begin, e_end, s)));
+  } else if (c->df64) {
+    ACMHD_DISPATCH_DM(c->dim, c->m,
+                      return (trace_launch<D_, M_, double, df64>(c->cdf, U, Tr, e_begin, e_end, s)));
   } else {
     ACMHD_DISPATCH_DM(c->dim, c->m,
-                      return (trace_launch<D_, M_, double>(c->cd, U, Tr, e_begin, e_end, s)));
+                      return (trace_launch<D_, M_, double, double>(c->cd, U, Tr, e_begin, e_end,
+                                                                  s)));
   }
   return cudaErrorInvalidValue;
 }

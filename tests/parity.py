@@ -34,9 +34,10 @@ from oracle import acmhd, fr
 from oracle.ops1d import Ops1D
 from paper_2107_14027_gb300 import workloads as W
 
-TOL = {32: 2e-5, 64: 1e-12}
-PLAIN_TOL = {32: 2e-5, 64: 1e-12}
-CANCEL_MIN = {32: 8 * 2.0 ** -24 / 2e-5, 64: 1e-3}
+# 65: FR_DF64 (FP64 storage, double-float arithmetic, unit roundoff ~2^-48)
+TOL = {32: 2e-5, 64: 1e-12, 65: 1e-12}
+PLAIN_TOL = {32: 2e-5, 64: 1e-12, 65: 1e-12}
+CANCEL_MIN = {32: 8 * 2.0 ** -24 / 2e-5, 64: 1e-3, 65: 8 * 2.0 ** -48 / 1e-12}
 
 
 def term_scale(U, mesh, order, prm, corr="dg"):

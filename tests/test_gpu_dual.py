@@ -40,9 +40,12 @@ def _vel_np(abi, ctx, V, d):
     return V[:, :ne].cpu().numpy().reshape(d, -1, ne)
 
 
+@pytest.mark.parametrize("precision", [64, 65])
 @pytest.mark.parametrize("bdf_order", [1, 2])
 @pytest.mark.parametrize("n,order", [((6, 5), 2), ((3, 4, 3), 2)])
-def test_pseudo_solve_matches_oracle_fixed_iterations(abi, n, order, bdf_order):
+def test_pseudo_solve_matches_oracle_fixed_iterations(abi, n, order, bdf_order, precision):
+    """FP64, and the double-float mode (FP64 storage, ~48-bit arithmetic in
+    the RHS kernels), against the oracle's pseudo-solve."""
     d = len(n)
     nv = 1 + d + d * d
     U0, mesh, prm, lo, hi = _case(n=n, order=order)
@@ -50,7 +53,7 @@ def test_pseudo_solve_matches_oracle_fixed_iterations(abi, n, order, bdf_order):
     Un = U0 + 1e-3 * rng.standard_normal(U0.shape)
     Unm1 = U0 + 2e-3 * rng.standard_normal(U0.shape)
     dt, dtau, iters = 1e-2, 1e-3, 12
-    ctx = abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, 64)
+    ctx = abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, precision)
     try:
         Ud = abi.pack_state(ctx, U0, 64)
         V = _vel_dev(abi, ctx, U0[1:1 + d], d, order)
@@ -166,15 +169,17 @@ def test_dual_steps_match_oracle(abi, precision):
             assert abs(res - reso) < 1e-3 * reso + 1e-5, (res, reso)
 
 
-def test_mixed_precision_step_hands_over_to_fp64(abi):
-    """The FP32 context iterates until tol_switch, then its FP64 twin takes the
-    residual (evaluated in FP64) to tol; the step agrees with an all-FP64
-    step at the same tolerance, and the FP64 velocity master carries over."""
+@pytest.mark.parametrize("twin", [64, 65])
+def test_mixed_precision_step_hands_over_to_fp64(abi, twin):
+    """The FP32 context iterates until tol_switch, then its FP64 twin (FP64 or
+    double-float arithmetic) takes the residual (evaluated in FP64) to tol;
+    the step agrees with an all-FP64 step at the same tolerance, and the
+    FP64 velocity master carries over."""
     n, order, d, nv = (6, 5), 2, 2, 7
     U0, mesh, prm, lo, hi = _case(n=n, order=order)
     dt, dtau, tol = 1e-2, 1e-2, 1e-5
     c32 = abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, 32)
-    c64 = abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, 64)
+    c64 = abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, twin)
     cref = abi.fr_create(n, lo, hi, order, nv, prm.zeta, prm.nu, prm.T, 64)
     try:
         U32 = abi.pack_state(c32, U0, 32)
