@@ -141,7 +141,9 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
   const bool valid = e < c.ne;
   const size_t Sd = c.stride;
 
-  // stage P and V of the tile (rows of E contiguous values)
+  // stage P and V of the tile (rows of E contiguous values); unrolled so
+  // that each thread has several independent loads in flight
+#pragma unroll 8
   for (int idx = tid; idx < (1 + D) * NP * E; idx += NW * 32) {
     const int row = idx / E, x = idx - row * E;
     sU[idx] = cvt<T>(__ldg(U + (size_t)row * Sd + e0 + x));

@@ -37,6 +37,7 @@ trace_kernel(const S* __restrict__ U, S* __restrict__ Tr, const FrConst<T> c, in
   const int sub = lane / E;
   if constexpr (PV) {
     // rows of E contiguous elements; the tile lies inside the padded stride
+#pragma unroll 8
     for (int idx = threadIdx.x; idx < (1 + D) * NP * E; idx += blockDim.x) {
       const int row = idx / E, x = idx - row * E;
       sPV[idx] = cvt<T>(__ldg(U + (size_t)row * c.stride + tile * E + x));
