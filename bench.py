@@ -281,8 +281,18 @@ def _err_vs_oracle(U, R, mesh_n, cfg, elems):
     ref = np.sqrt(np.mean(R_ref ** 2, axis=(1, 2)))
     scale = np.sqrt(np.mean(B ** 2, axis=(1, 2)))
     names = ["P", "u", "v", "w"] + [f"{g}{x}" for g in "qrs" for x in "xyz"]
+    # the plain relative error means something only where the result does not
+    # cancel far below its summed terms: ||R|| / ||B|| >= 8 u / tol (FP32:
+    # u = 2^-24, tol = 2e-5); other rows (the exact-gradient auxiliary rows,
+    # P of the divergence-free field) are held to the scaled bound alone
+    ratio = ref / np.maximum(scale, 1e-300)
+    thr = 8 * 2.0 ** -24 / 2e-5
+    plain = diff / np.maximum(ref, 1e-300)
     return {"elements": int(len(elems)), "oracle": "FP64 per-element (dense) path",
-            "plain": {k: float(v) for k, v in zip(names, diff / np.maximum(ref, 1e-300))},
+            "plain": {k: (float(v) if r >= thr else None)
+                      for k, v, r in zip(names, plain, ratio)},
+            "plain_rows_threshold": {"R_over_B_min": thr,
+                                     "R_over_B": {k: float(r) for k, r in zip(names, ratio)}},
             "scaled": {k: float(v) for k, v in zip(names, diff / np.maximum(scale, 1e-300))},
             "max_scaled": float(np.max(diff / np.maximum(scale, 1e-300))),
             "oracle_s": t_ref}
@@ -890,8 +900,10 @@ def run_mlp(args):
     """The network's GEMMs at the inference shapes of the dual-time workload
     (p = 4, 48^3: 110,592 elements, 4875 -> 256 -> 256 -> 1625 features):
     C[N x M] = W[N x K] . X[K x M] in BF16 with FP32 accumulation through
-    fr_gemm_bf16 (the library's tensor-core kernel), against the measured
-    cuBLAS BF16 peak."""
+    fr_gemm_bf16, with the tensor-memory kernel (tcgen05, the default) and the
+    warp-level mma.sync kernel, against the measured cuBLAS BF16 peak; then
+    the backward orientations at the training shapes (5,000 samples), which
+    the mma.sync kernels serve."""
     import torch
     from paper_2107_14027_gb300 import abi
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -899,26 +911,53 @@ def run_mlp(args):
     peak = float(pk.get("bf16_tflops", 1900.0))
     stream = torch.cuda.current_stream()
     M = 110592
-    rows, tot_flop, tot_s = [], 0.0, 0.0
-    for N, K in ((256, 4880), (256, 256), (1625, 256)):
-        W = (torch.randn(N, K, device="cuda") * 0.05).to(torch.bfloat16)
-        X = torch.randn(K, M, device="cuda").to(torch.bfloat16)
-        C = torch.empty(N, M, device="cuda", dtype=torch.float32)
-        fn = lambda: abi.fr_gemm_bf16(0, 0, N, M, K, W, K, X, M, C, M, stream)
+    out = {}
+    for kind, label in ((abi.FR_GEMM_AUTO, "tcgen05"), (abi.FR_GEMM_MMA_SYNC, "mma_sync")):
+        abi.fr_gemm_set_kernel(kind)
+        rows, tot_flop, tot_s = [], 0.0, 0.0
+        for N, K, lda in ((256, 4875, 4880), (256, 256, 256), (1625, 256, 256)):
+            W = torch.zeros(N, lda, device="cuda", dtype=torch.bfloat16)
+            W[:, :K] = (torch.randn(N, K, device="cuda") * 0.05).to(torch.bfloat16)
+            X = torch.randn(K, M, device="cuda").to(torch.bfloat16)
+            C = torch.empty(N, M, device="cuda", dtype=torch.float32)
+            fn = lambda: abi.fr_gemm_bf16(0, 0, N, M, K, W, lda, X, M, C, M, stream)
+            t = _time_loop(fn, stream, args.steps, args.warmup, torch) / args.steps
+            abi.fr_gemm_check(stream)
+            ref = (W[:, :K].float() @ X.float())
+            err = float((C - ref).abs().max() / ref.abs().max())
+            flop = 2.0 * N * M * K
+            rows.append({"N": N, "M": M, "K": K, "ms": 1e3 * t, "tflops": flop / t / 1e12,
+                         "frac_of_measured_bf16": flop / t / 1e12 / peak,
+                         "hbm_bytes_min": 2.0 * K * M + 2.0 * N * lda + 4.0 * N * M,
+                         "max_rel_err_vs_fp32": err})
+            tot_flop += flop
+            tot_s += t
+            del W, X, C, ref
+        out[label] = {"tflops": tot_flop / tot_s / 1e12, "ms": 1e3 * tot_s, "layers": rows}
+    abi.fr_gemm_set_kernel(abi.FR_GEMM_AUTO)
+    # backward products of one training step at 5,000 samples (mma.sync)
+    n, bw = 5000, []
+    for name, am, bm, N, Mo, K in (("dW1", 0, 1, 256, 4875, n), ("dH1", 1, 0, 256, n, 256),
+                                    ("dW3", 0, 1, 1625, 256, n), ("dH2", 1, 0, 256, n, 1625)):
+        A = (torch.randn(N, K, device="cuda") if am == 0 else torch.randn(K, N, device="cuda")).to(
+            torch.bfloat16)
+        B = (torch.randn(K, Mo, device="cuda") if bm == 0 else torch.randn(Mo, K, device="cuda")).to(
+            torch.bfloat16)
+        C = torch.empty(N, Mo, device="cuda", dtype=torch.float32)
+        lda = K if am == 0 else N
+        ldb = Mo if bm == 0 else K
+        fn = lambda: abi.fr_gemm_bf16(am, bm, N, Mo, K, A, lda, B, ldb, C, Mo, stream)
         t = _time_loop(fn, stream, args.steps, args.warmup, torch) / args.steps
-        ref = (W.float() @ X.float())
-        err = float((C - ref).abs().max() / ref.abs().max())
-        flop = 2.0 * N * M * K
-        rows.append({"N": N, "M": M, "K": K, "ms": 1e3 * t, "tflops": flop / t / 1e12,
-                     "frac_of_measured_bf16": flop / t / 1e12 / peak, "max_rel_err_vs_fp32": err})
-        tot_flop += flop
-        tot_s += t
-        del W, X, C, ref
+        flop = 2.0 * N * Mo * K
+        bw.append({"gemm": name, "N": N, "M": Mo, "K": K, "ms": 1e3 * t,
+                   "tflops": flop / t / 1e12, "frac_of_measured_bf16": flop / t / 1e12 / peak})
+        del A, B, C
     print(json.dumps({"metric": "BF16 GEMM TFLOP/s, MLP inference shapes", "unit": "TFLOP/s",
-                      "value": tot_flop / tot_s / 1e12, "higher_is_better": True, "n_gpus": 1,
+                      "value": out["tcgen05"]["tflops"], "higher_is_better": True, "n_gpus": 1,
                       "dtype": "bf16", "data": "synthetic", "steps": args.steps,
                       "warmup": args.warmup, "peak_tflops": peak, "peak_source": "measured",
-                      "kernel": "mma.sync m16n8k16 BF16, 64x64x32 CTA tiles", "gemms": rows}))
+                      "kernel": "tcgen05.mma kind::f16 128x256 tiles, TMEM accumulators, TMA",
+                      "inference": out, "backward_training_5000": bw}))
 
 
 def run_rk(args):

@@ -30,7 +30,7 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", 
            "fr_mlp_train_step", "fr_mlp_save", "fr_mlp_load", "fr_fma_probe",
            "fr_pmg_create", "fr_pmg_destroy", "fr_pmg_set_cycle", "fr_pmg_set_dtau",
            "fr_pmg_solve", "fr_pmg_set_anderson", "fr_mlp_set_training",
-           "fr_mlp_validation_loss"]
+           "fr_mlp_validation_loss", "fr_gemm_set_kernel", "fr_gemm_check"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -118,6 +118,8 @@ def _lib():
         lib.fr_mlp_load.argtypes = [vp, ctypes.c_char_p, i32, ctypes.POINTER(vp)]
         lib.fr_gemm_bf16.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.c_longlong, vp,
                                      ctypes.c_longlong, vp, ctypes.c_longlong, vp]
+        lib.fr_gemm_set_kernel.argtypes = [i32]
+        lib.fr_gemm_check.argtypes = [vp]
         lib.fr_strerror.argtypes = [i32]
         lib.fr_strerror.restype = ctypes.c_char_p
         lib.fr_last_error.argtypes = []
@@ -446,6 +448,17 @@ def fr_gemm_bf16(amode, bmode, N, M, K, A, lda, B, ldb, C, ldc, stream=None):
     _check(_lib().fr_gemm_bf16(int(amode), int(bmode), int(N), int(M), int(K), _ptr(A), int(lda),
                                _ptr(B), int(ldb), _ptr(C), int(ldc), _stream(stream)),
            "fr_gemm_bf16")
+
+
+FR_GEMM_AUTO, FR_GEMM_MMA_SYNC = 0, 1
+
+
+def fr_gemm_set_kernel(kind):
+    _check(_lib().fr_gemm_set_kernel(int(kind)), "fr_gemm_set_kernel")
+
+
+def fr_gemm_check(stream=None):
+    _check(_lib().fr_gemm_check(_stream(stream)), "fr_gemm_check")
 
 
 def fr_fma_probe(precision, iters, out, stream=None):

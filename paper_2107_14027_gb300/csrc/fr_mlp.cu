@@ -50,6 +50,8 @@ struct fr_mlp {
   __nv_bfloat16* Xi;     // inference features [K x stride]
   __nv_bfloat16 *Hi1, *Hi2;
   float* Yc;             // [NO x stride] scaled corrections
+  __nv_bfloat16* w1p;    // [H x Kp] BF16 W1 with rows padded to a multiple of 8
+  int Kp;                //   values (16 bytes), the tensor-memory GEMM's TMA pitch
 };
 
 namespace {
@@ -119,7 +121,15 @@ GemmArgs gemm(int N, int M, int K, const __nv_bfloat16* A, long long lda, const 
 int forward(fr_mlp* q, const __nv_bfloat16* X, long long ld, int cols, float* Z1,
             __nv_bfloat16* H1, float* Z2, __nv_bfloat16* H2, float* Y, const float* row_scale,
             cudaStream_t s) {
-  GemmArgs g = gemm(q->H, cols, q->K, q->pb[0], q->K, X, ld);
+  const __nv_bfloat16* W1 = q->pb[0];
+  long long ldw1 = q->K;
+  if (q->w1p) {
+    int st = st_of(acmhd::launch_pad_rows(q->pb[0], q->H, q->K, q->w1p, q->Kp, s), "mlp pad W1");
+    if (st != FR_OK) return st;
+    W1 = q->w1p;
+    ldw1 = q->Kp;
+  }
+  GemmArgs g = gemm(q->H, cols, q->K, W1, ldw1, X, ld);
   g.bias = q->p[1];
   g.C = Z1;
   g.ldc = ld;
@@ -278,6 +288,8 @@ int fr_mlp_create(fr_ctx* c, int hidden, int capacity, unsigned long long seed, 
        (st = dalloc(&q->partial, (size_t)q->nparts)) || (st = dalloc(&q->loss, 1)) ||
        (st = dalloc(&q->val_loss, 1))))
     ;
+  q->Kp = (q->K + 7) / 8 * 8;
+  if (st == FR_OK && q->Kp != q->K) st = dalloc(&q->w1p, (size_t)q->H * q->Kp);
   if (st == FR_OK) st = st_of(cudaDeviceSynchronize(), "mlp init");
   if (st != FR_OK) {
     fr_mlp_destroy(q);
@@ -300,7 +312,7 @@ void fr_mlp_destroy(fr_mlp* q) {
   void* bufs[] = {q->in_scale, q->in_scale_inv, q->out_scale, q->out_scale_inv, q->Xs, q->Ts,
                   q->elems, q->Z1, q->Z2, q->Y, q->dY, q->dZ2, q->dZ1, q->H1b, q->H2b, q->dYb,
                   q->dZ2b, q->dZ1b, q->partial, q->loss, q->val_loss, q->Xi, q->Hi1, q->Hi2,
-                  q->Yc};
+                  q->Yc, q->w1p};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete q;
@@ -688,6 +700,28 @@ int fr_gemm_bf16(int amode, int bmode, int N, int M, int K, const void* A, long 
   g.C = C;
   g.ldc = ldc;
   return st_of(acmhd::launch_gemm(amode, bmode, g, static_cast<cudaStream_t>(stream)), "gemm");
+}
+
+int fr_gemm_set_kernel(int kind) {
+  if (kind != FR_GEMM_AUTO && kind != FR_GEMM_MMA_SYNC) return FR_EINVAL;
+  acmhd::set_gemm_kernel(kind == FR_GEMM_AUTO ? acmhd::GEMM_KERNEL_AUTO
+                                              : acmhd::GEMM_KERNEL_MMA_SYNC);
+  return FR_OK;
+}
+
+int fr_gemm_check(void* stream) {
+  int st = st_of(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "gemm");
+  if (st != FR_OK) return st;
+  const int code = acmhd::gemm_tc_status();
+  if (code != 0) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "tensor-memory GEMM: a bounded wait gave up (code %d); its output is invalid",
+                  code);
+    acmhd::set_last_error(msg);
+    return FR_ECUDA;
+  }
+  return FR_OK;
 }
 
 }  // extern "C"

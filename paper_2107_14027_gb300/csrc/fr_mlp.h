@@ -43,7 +43,23 @@ struct MlpHist {
   int dim, nv, npts, ne, stride;
 };
 
+// Which kernel serves the forward orientation (A_NK x B_KM): AUTO takes the
+// tcgen05 kernel (k_gemm_tc.cu) whenever its TMA alignment rules hold (both
+// operands 16-byte aligned with row pitches a multiple of 8 values), the
+// mma.sync kernels otherwise; MMA_SYNC always takes the mma.sync kernels.
+enum { GEMM_KERNEL_AUTO = 0, GEMM_KERNEL_MMA_SYNC = 1 };
+void set_gemm_kernel(int mode);
+int get_gemm_kernel();
+bool gemm_tc_eligible(int amode, int bmode, const GemmArgs& g);
+cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t s);
+// Error code left by a tcgen05 GEMM whose bounded wait gave up (0: none;
+// reading clears it; synchronises the device).
+int gemm_tc_status();
+
 cudaError_t launch_gemm(int amode, int bmode, const GemmArgs& g, cudaStream_t s);
+// dst[r][0..cols) = src[r][0..cols), dst rows padded with zeros to ldd
+cudaError_t launch_pad_rows(const __nv_bfloat16* src, int rows, int cols, __nv_bfloat16* dst,
+                            int ldd, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gather_features(const MlpHist<T>& h, const int* elems, int ncols,
                                    const float* inv_scale, int Kpad, __nv_bfloat16* X,

@@ -523,6 +523,17 @@ apply_guess_kernel(const MlpHist<T> h, const float* __restrict__ Yc, long long l
   }
 }
 
+__global__ void __launch_bounds__(256)
+pad_rows_kernel(const __nv_bfloat16* __restrict__ src, int rows, int cols,
+                __nv_bfloat16* __restrict__ dst, int ldd) {
+  const long long total = (long long)rows * ldd;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / ldd, c = i % ldd;
+    dst[i] = c < cols ? src[r * cols + c] : __float2bfloat16(0.0f);
+  }
+}
+
 int blocks_for(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
@@ -531,6 +542,7 @@ int blocks_for(long long n) {
 }  // namespace
 
 cudaError_t launch_gemm(int amode, int bmode, const GemmArgs& g, cudaStream_t s) {
+  if (gemm_tc_eligible(amode, bmode, g)) return launch_gemm_tc(g, s);
   const auto a16 = [](const void* p, long long ld) {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 8 == 0;
   };
@@ -555,6 +567,12 @@ cudaError_t launch_gemm(int amode, int bmode, const GemmArgs& g, cudaStream_t s)
     gemm_bf16_kernel<GEMM_A_KN, GEMM_B_MK><<<grid, GEMM_THREADS, 0, s>>>(g);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_rows(const __nv_bfloat16* src, int rows, int cols, __nv_bfloat16* dst,
+                            int ldd, cudaStream_t s) {
+  pad_rows_kernel<<<blocks_for((long long)rows * ldd), 256, 0, s>>>(src, rows, cols, dst, ldd);
   return cudaGetLastError();
 }
 
