@@ -34,6 +34,7 @@
 #include <cstdint>
 #include <atomic>
 
+#include "async_copy.cuh"
 #include "fr_mlp.h"
 #include "per_device_once.h"
 
@@ -62,54 +63,6 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) |
                            (uint32_t(TBN >> 3) << 17) | (uint32_t(TBM >> 4) << 24);
 
 __device__ int g_tc_error = 0;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t now_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for the phase of parity `parity` to complete.  Gives up (false) when
-// another role has given up (abort set) or after WAIT_LIMIT_NS.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort) {
-  const uint64_t t0 = now_ns();
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 63u) == 63u) {
-      if (abort && *abort) return false;
-      if (now_ns() - t0 > WAIT_LIMIT_NS) return false;
-    }
-  }
-}
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
                                             int x, int y) {
@@ -174,6 +127,60 @@ __device__ void give_up(volatile int* abort, int code) {
   atomicMax(&g_tc_error, code);
 }
 
+// Epilogue flags: which parts of GemmArgs a launch uses, so that the code of
+// the 32-row chunk carries no run-time tests per value.  EP_ANY tests them
+// at run time (combinations the network does not use).
+enum : int {
+  EP_BIAS = 1, EP_MASK = 2, EP_RSCALE = 4, EP_C = 8, EP_ACC = 16, EP_CB = 32, EP_RELU = 64,
+  EP_ANY = 128
+};
+
+template <int FL>
+__device__ __forceinline__ bool ep_has(int bit, bool runtime) {
+  return (FL & EP_ANY) ? runtime : (FL & bit) != 0;
+}
+
+// 32 output rows n0 .. n0+31 of sample m (this thread's TMEM lane), values
+// v[j] = D[m][n0 + j]: z = v + bias[n]; z = 0 where mask[n][m] <= 0;
+// z *= row_scale[n / rows_per_scale]; C[n][m] = z (or += z); Cb[n][m] =
+// bf16(relu ? max(z, 0) : z).  Per-row operands are loaded once per chunk
+// (lane j holds row n0 + j) and broadcast by shuffles; for each row the warp
+// writes 32 consecutive samples.
+template <int FL>
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs& g, const uint32_t (&v)[32], int n0,
+                                               long long m, bool m_ok, int lane) {
+  const bool has_bias = ep_has<FL>(EP_BIAS, g.bias != nullptr);
+  const bool has_mask = ep_has<FL>(EP_MASK, g.mask != nullptr);
+  const bool has_rs = ep_has<FL>(EP_RSCALE, g.row_scale != nullptr);
+  const bool has_c = ep_has<FL>(EP_C, g.C != nullptr);
+  const bool acc = ep_has<FL>(EP_ACC, g.accumulate != 0);
+  const bool has_cb = ep_has<FL>(EP_CB, g.Cb != nullptr);
+  const bool relu = ep_has<FL>(EP_RELU, g.relu != 0);
+  const int jmax = g.N - n0 < 32 ? g.N - n0 : 32;
+  const int nl = n0 + (lane < jmax ? lane : 0);
+  const float bias_l = has_bias ? g.bias[nl] : 0.0f;
+  const float rs_l = has_rs ? g.row_scale[nl / g.rows_per_scale] : 1.0f;
+  float* cp = has_c ? g.C + (long long)n0 * g.ldc + m : nullptr;
+  __nv_bfloat16* cbp = has_cb ? g.Cb + (long long)n0 * g.ldcb + m : nullptr;
+  const float* mp = has_mask ? g.mask + (long long)n0 * g.ldm + m : nullptr;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    float z = __uint_as_float(v[j]);
+    if (has_bias) z += __shfl_sync(0xffffffffu, bias_l, j);
+    const float rs = has_rs ? __shfl_sync(0xffffffffu, rs_l, j) : 1.0f;
+    if (j < jmax && m_ok) {
+      if (has_mask && !(mp[0] > 0.0f)) z = 0.0f;
+      if (has_rs) z *= rs;
+      if (has_c) *cp = acc ? *cp + z : z;
+      if (has_cb) *cbp = __float2bfloat16(relu ? fmaxf(z, 0.0f) : z);
+    }
+    if (has_c) cp += g.ldc;
+    if (has_cb) cbp += g.ldcb;
+    if (has_mask) mp += g.ldm;
+  }
+}
+
+template <int FL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
                const GemmArgs g) {
@@ -182,7 +189,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   __shared__ uint32_t tmem_slot;
   volatile int* abort = &abort_flag;
 
-  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t raw = smem_u32addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
   const uint32_t bars = base + TSTAGES * STAGE_BYTES;
   auto full = [&](int s) { return bars + 8u * s; };
@@ -208,11 +215,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     }
     mbar_init(drain, 1);
     abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(&tmem_slot)),
+                     smem_u32addr(&tmem_slot)),
                  "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -233,13 +240,13 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         const int nt = (int)(t % n_tiles), mt = (int)(t / n_tiles);
         for (int kb = 0; kb < nk; ++kb) {
-          if (!mbar_wait(empty(s), ph ^ 1u, abort)) {
+          if (!mbar_wait(empty(s), ph ^ 1u, WAIT_LIMIT_NS, abort)) {
             give_up(abort, 1);
             ok = false;
             break;
           }
           const uint32_t xs = base + s * STAGE_BYTES, ws = xs + X_BYTES;
-          mbar_expect_tx(full(s), STAGE_BYTES);
+          mbar_arrive_expect_tx(full(s), STAGE_BYTES);
           tma_load_2d(xs, &tmX, full(s), mt * TBM, kb * TBK);
           tma_load_2d(xs + X_BOX, &tmX, full(s), mt * TBM + 64, kb * TBK);
           tma_load_2d(ws, &tmW, full(s), kb * TBK, nt * TBN);
@@ -252,7 +259,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       }
       // copies in flight land before the CTA may exit (bounded)
       for (int i = 0; i < TSTAGES; ++i)
-        if (armed[i] >= 0 && !mbar_wait(full(i), (uint32_t)armed[i], nullptr)) give_up(abort, 2);
+        if (armed[i] >= 0 && !mbar_wait(full(i), (uint32_t)armed[i], WAIT_LIMIT_NS)) give_up(abort, 2);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -263,14 +270,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
         const int b = i & 1;
         const uint32_t bph = (uint32_t)(i >> 1) & 1u;
-        if (!mbar_wait(tempty(b), bph ^ 1u, abort)) {
+        if (!mbar_wait(tempty(b), bph ^ 1u, WAIT_LIMIT_NS, abort)) {
           give_up(abort, 3);
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(b * TBN);
         for (int kb = 0; kb < nk; ++kb) {
-          if (!mbar_wait(full(s), ph, abort)) {
+          if (!mbar_wait(full(s), ph, WAIT_LIMIT_NS, abort)) {
             give_up(abort, 4);
             ok = false;
             break;
@@ -295,7 +302,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       }
       // every MMA issued has finished before TMEM is freed (bounded)
       tc_commit(drain);
-      if (!mbar_wait(drain, 0, nullptr)) give_up(abort, 5);
+      if (!mbar_wait(drain, 0, WAIT_LIMIT_NS)) give_up(abort, 5);
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its samples) and
@@ -309,7 +316,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
       // tcgen05.ld is a warp-wide instruction
       int ok = 0;
       if (lane == 0) {
-        ok = mbar_wait(tfull(b), bph, abort) ? 1 : 0;
+        ok = mbar_wait(tfull(b), bph, WAIT_LIMIT_NS, abort) ? 1 : 0;
         if (!ok) give_up(abort, 6);
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
@@ -324,29 +331,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         if (n0 >= g.N) break;
         uint32_t v[32];
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TBN + col), v);
-        // row_scale index n / rows_per_scale, stepped along the 32 rows
-        int rs_i = 0, rs_r = 0;
-        if (g.row_scale) {
-          rs_i = n0 / g.rows_per_scale;
-          rs_r = n0 - rs_i * g.rows_per_scale;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const long long n = n0 + j;
-          const float rs = g.row_scale ? g.row_scale[rs_i] : 1.0f;
-          if (g.row_scale && ++rs_r == g.rows_per_scale) {
-            rs_r = 0;
-            ++rs_i;
-          }
-          if (n < g.N && m_ok) {
-            float z = __uint_as_float(v[j]);
-            if (g.bias) z += g.bias[n];
-            if (g.mask && !(g.mask[n * g.ldm + m] > 0.0f)) z = 0.0f;
-            if (g.row_scale) z *= rs;
-            if (g.C) g.C[n * g.ldc + m] = g.accumulate ? g.C[n * g.ldc + m] + z : z;
-            if (g.Cb) g.Cb[n * g.ldcb + m] = __float2bfloat16(g.relu ? fmaxf(z, 0.0f) : z);
-          }
-        }
+        epilogue_chunk<FL>(g, v, n0, m, m_ok, lane);
       }
       tc_fence_before();
       __syncwarp();
@@ -398,7 +383,6 @@ bool make_map(CUtensorMap* map, const void* ptr, long long inner, long long oute
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-PerDeviceOnce g_tc_attr;
 std::atomic<int> g_tc_mode{GEMM_KERNEL_AUTO};
 
 }  // namespace
@@ -416,17 +400,29 @@ bool gemm_tc_eligible(int amode, int bmode, const GemmArgs& g) {
          g.ldb >= g.M && encode_fn() != nullptr;
 }
 
+namespace {
+
+template <int FL>
+cudaError_t launch_tc(const CUtensorMap& mx, const CUtensorMap& mw, const GemmArgs& g, int grid,
+                      cudaStream_t s) {
+  static PerDeviceOnce attr;  // per instance: the attribute is per device and kernel
+  const int st = attr.run([](int* d) { return cudaGetDevice(d); },
+                          [] {
+                            return cudaFuncSetAttribute(
+                                gemm_tc_kernel<FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_BYTES);
+                          });
+  if (st != 0) return static_cast<cudaError_t>(st);
+  gemm_tc_kernel<FL><<<grid, TC_THREADS, SMEM_BYTES, s>>>(mx, mw, g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t s) {
   CUtensorMap mx, mw;
   if (!make_map(&mx, g.B, g.M, g.K, g.ldb, TBK) || !make_map(&mw, g.A, g.K, g.N, g.lda, TBN))
     return cudaErrorInvalidValue;
-  int st = g_tc_attr.run([](int* d) { return cudaGetDevice(d); },
-                         [] {
-                           return cudaFuncSetAttribute(gemm_tc_kernel,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       SMEM_BYTES);
-                         });
-  if (st != 0) return static_cast<cudaError_t>(st);
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -434,8 +430,19 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t s) {
   const long long tiles =
       (long long)((g.N + TBN - 1) / TBN) * (long long)((g.M + TBM - 1) / TBM);
   const int grid = (int)(tiles < sms ? tiles : sms);
-  gemm_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(mx, mw, g);
-  return cudaGetLastError();
+  const int fl = (g.bias ? EP_BIAS : 0) | (g.mask ? EP_MASK : 0) | (g.row_scale ? EP_RSCALE : 0) |
+                 (g.C ? EP_C : 0) | (g.C && g.accumulate ? EP_ACC : 0) | (g.Cb ? EP_CB : 0) |
+                 (g.Cb && g.relu ? EP_RELU : 0);
+  // the combinations of the network's forward pass and of fr_gemm_bf16
+  switch (fl) {
+    case EP_C: return launch_tc<EP_C>(mx, mw, g, grid, s);
+    case EP_BIAS | EP_C | EP_CB | EP_RELU:
+      return launch_tc<EP_BIAS | EP_C | EP_CB | EP_RELU>(mx, mw, g, grid, s);
+    case EP_BIAS | EP_CB | EP_RELU: return launch_tc<EP_BIAS | EP_CB | EP_RELU>(mx, mw, g, grid, s);
+    case EP_BIAS | EP_C: return launch_tc<EP_BIAS | EP_C>(mx, mw, g, grid, s);
+    case EP_BIAS | EP_C | EP_RSCALE: return launch_tc<EP_BIAS | EP_C | EP_RSCALE>(mx, mw, g, grid, s);
+    default: return launch_tc<EP_ANY>(mx, mw, g, grid, s);
+  }
 }
 
 int gemm_tc_status() {

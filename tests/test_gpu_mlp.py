@@ -117,9 +117,13 @@ MLP_CASES = [
 ]
 
 
+@pytest.mark.parametrize("kind", ["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("n,order,H,S", MLP_CASES)
-def test_loss_gradients_adam_and_prediction_match_oracle(abi, n, order, H, S):
+def test_loss_gradients_adam_and_prediction_match_oracle(abi, n, order, H, S, kind):
+    """Both GEMM kernels of the forward products (the tensor-memory kernel,
+    the default, and the warp-level mma.sync kernel) against the oracle."""
     d = len(n)
+    abi.fr_gemm_set_kernel(abi.FR_GEMM_AUTO if kind == "tcgen05" else abi.FR_GEMM_MMA_SYNC)
     ctx, Ud, levels, nv = _history_case(abi, n=n, order=order, dtau=1e-2 if d == 2 else 2e-3)
     net = abi.fr_mlp_create(ctx, H, S, seed=7)
     try:
@@ -204,7 +208,9 @@ def test_loss_gradients_adam_and_prediction_match_oracle(abi, n, order, H, S):
         stride, _, _ = abi.fr_layout(ctx)
         V = Vg[:, :ne].cpu().numpy().reshape(d, -1, ne)
         np.testing.assert_allclose(V, G[1:1 + d], rtol=0, atol=1e-12)
+        abi.fr_gemm_check()
     finally:
+        abi.fr_gemm_set_kernel(abi.FR_GEMM_AUTO)
         abi.fr_mlp_destroy(net)
         abi.fr_destroy(ctx)
 
