@@ -141,6 +141,48 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
   const bool valid = e < c.ne;
   const size_t Sd = c.stride;
 
+  int nb[3][2];
+  neighbours<D>(valid ? e : 0, c.n, nb);
+
+  // The operands of one line that come from global memory: the auxiliary
+  // slots along the line and the neighbours' traces at its two faces.  In
+  // the x phase a neighbour inside the lane group is served by a shuffle
+  // below, so only the others are read from memory.
+  struct LineOps {
+    T aux[D][M];
+    T lo[NS], hi[NS];
+  };
+  auto line_of = [&](int l0) { return l0 + sub < NL ? l0 + sub : NL - 1; };
+  auto load_ops = [&](int a, int l0, LineOps& o) {
+    const int l = line_of(l0);
+    const bool act = valid && (l0 + sub < NL);
+#pragma unroll
+    for (int t = 0; t < M; ++t) {
+      const int pt = line_pt<D, M>(a, l, t);
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+        o.aux[i][t] = cvt<T>(__ldg(U + ((size_t)aux_var<D>(i, a) * NP + pt) * Sd + e));
+    }
+    const bool lo_mem = (a != 0) || (act && !x_pair_on_chip(nb[0][0], e, E));
+    const bool hi_mem = (a != 0) || (act && !x_pair_on_chip(e, nb[0][1], E));
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      o.lo[s] = lo_mem ? cvt<T>(__ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd +
+                                       nb[a][0]))
+                       : T(0);
+      o.hi[s] = hi_mem ? cvt<T>(__ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * Sd +
+                                       nb[a][1]))
+                       : T(0);
+    }
+  };
+
+  // The first line of each axis phase has its global operands requested
+  // before the CTA barrier that opens the phase (they do not depend on it),
+  // so their latency overlaps the staging of P and V and the barrier waits;
+  // every other line issues its loads at its start.
+  LineOps pre;
+  load_ops(0, warp * SUB, pre);
+
   // stage P and V of the tile (rows of E contiguous values); unrolled so
   // that each thread has several independent loads in flight
 #pragma unroll 8
@@ -148,8 +190,6 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
     const int row = idx / E, x = idx - row * E;
     sU[idx] = cvt<T>(__ldg(U + (size_t)row * Sd + e0 + x));
   }
-  int nb[3][2];
-  neighbours<D>(valid ? e : 0, c.n, nb);
   __syncthreads();
 
 #pragma unroll
@@ -159,6 +199,13 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
       const bool lvalid = l0 + sub < NL;
       const int l = lvalid ? l0 + sub : NL - 1;
       const bool act = valid && lvalid;
+      LineOps ops;
+      if (l0 == warp * SUB)
+        ops = pre;
+      else
+        load_ops(a, l0, ops);
+      const bool lo_mem = (a != 0) || (act && !x_pair_on_chip(nb[0][0], e, E));
+      const bool hi_mem = (a != 0) || (act && !x_pair_on_chip(e, nb[0][1], E));
       // slot values along the line
       T u[NS][M];
 #pragma unroll
@@ -167,23 +214,13 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
 #pragma unroll
         for (int s = 0; s <= D; ++s) u[s][t] = sU[(s * NP + pt) * E + el];
 #pragma unroll
-        for (int i = 0; i < D; ++i)
-          u[1 + D + i][t] = cvt<T>(__ldg(U + ((size_t)aux_var<D>(i, a) * NP + pt) * Sd + e));
+        for (int i = 0; i < D; ++i) u[1 + D + i][t] = ops.aux[i][t];
       }
-      // neighbour traces: issued right after the line's own loads.  In the
-      // x phase a neighbour inside the lane group is served by a shuffle
-      // below, so only the others are read from memory.
-      const bool lo_mem = (a != 0) || (act && !x_pair_on_chip(nb[0][0], e, E));
-      const bool hi_mem = (a != 0) || (act && !x_pair_on_chip(e, nb[0][1], E));
       T nb_lo[NS], nb_hi[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        nb_lo[s] = lo_mem ? cvt<T>(__ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd +
-                                          nb[a][0]))
-                          : T(0);
-        nb_hi[s] = hi_mem ? cvt<T>(__ldg(Tr + (((size_t)(2 * a) * NS + s) * NL + l) * Sd +
-                                          nb[a][1]))
-                          : T(0);
+        nb_lo[s] = ops.lo[s];
+        nb_hi[s] = ops.hi[s];
       }
       // own traces, and the common fluxes at the two faces (stage 4).  On
       // the y and z faces the trace kernel (or the previous fused stage)
@@ -276,6 +313,7 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
         }
       }
     }
+    if (a + 1 < D) load_ops(a + 1, warp * SUB, pre);
     __syncthreads();  // partial sums complete before the next axis; smem free after the last
   }
   if constexpr (Out::kStage) {
