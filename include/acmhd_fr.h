@@ -446,14 +446,13 @@ int fr_mlp_load(fr_ctx* ctx, const char* path, int capacity, fr_mlp** out);
 int fr_gemm_bf16(int amode, int bmode, int N, int M, int K, const void* A, long long lda,
                  const void* B, long long ldb, float* C, long long ldc, void* stream);
 
-/* Kernel choice for the GEMMs of the forward orientation (amode 0, bmode 0:
- * every layer of the network's forward pass and inference), process-wide.
+/* Kernel choice for the network's GEMMs (fr_gemm_bf16 and the MLP's
+ * forward and backward products, every orientation), process-wide.
  * FR_GEMM_AUTO (the default): the fifth-generation tensor-core kernel
  * (tcgen05.mma with the accumulators in tensor memory, operands brought in
  * by TMA) whenever A and B start on 16-byte boundaries and lda, ldb are
  * multiples of 8; the warp-level mma.sync kernels otherwise.
- * FR_GEMM_MMA_SYNC: always the mma.sync kernels (for comparison).  The other
- * orientations (the backward products) always take the mma.sync kernels.
+ * FR_GEMM_MMA_SYNC: always the mma.sync kernels (for comparison).
  * FR_EINVAL for another value. */
 enum { FR_GEMM_AUTO = 0, FR_GEMM_MMA_SYNC = 1 };
 int fr_gemm_set_kernel(int kind);

@@ -43,15 +43,15 @@ struct MlpHist {
   int dim, nv, npts, ne, stride;
 };
 
-// Which kernel serves the forward orientation (A_NK x B_KM): AUTO takes the
-// tcgen05 kernel (k_gemm_tc.cu) whenever its TMA alignment rules hold (both
-// operands 16-byte aligned with row pitches a multiple of 8 values), the
-// mma.sync kernels otherwise; MMA_SYNC always takes the mma.sync kernels.
+// Which kernel serves a GEMM: AUTO takes the tcgen05 kernel (k_gemm_tc.cu,
+// every orientation) whenever its TMA alignment rules hold (both operands
+// 16-byte aligned with row pitches a multiple of 8 values), the mma.sync
+// kernels otherwise; MMA_SYNC always takes the mma.sync kernels.
 enum { GEMM_KERNEL_AUTO = 0, GEMM_KERNEL_MMA_SYNC = 1 };
 void set_gemm_kernel(int mode);
 int get_gemm_kernel();
 bool gemm_tc_eligible(int amode, int bmode, const GemmArgs& g);
-cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t s);
+cudaError_t launch_gemm_tc(int amode, int bmode, const GemmArgs& g, cudaStream_t s);
 // Error code left by a tcgen05 GEMM whose bounded wait gave up (0: none;
 // reading clears it; synchronises the device).
 int gemm_tc_status();

@@ -1,22 +1,27 @@
-// Fifth-generation tensor-core GEMM for the forward orientation of the
-// per-element MLP (no counterpart in the paper; see fr_mlp.cu):
+// Fifth-generation tensor-core GEMM of the per-element MLP (no counterpart in
+// the paper; see fr_mlp.cu):
 //
-//     C[N x M] = W[N x K] . X[K x M]      (W rows of k, X rows of m)
+//     C[N x M] = W[N x K] . X[K x M]
 //
 // N output features, K inputs, M samples (elements), the sample index
 // contiguous as in the solver state.  The tensor cores compute the
 // transposed product D[m][n] = sum_k X[k][m] W[n][k] with D in tensor memory
 // (TMEM), so one accumulator lane holds one sample and the epilogue writes
-// each output row as 128-byte coalesced stores.
+// each output row as 128-byte coalesced stores.  The forward products read
+// W as [n][k] and X as [k][m]; the backward products read X as [m][k] (the
+// weight gradients dW = dZ . H^T, X = H) or W as [k][n] (W^T dY): the MMA
+// takes either operand K-major or MN-major, so all four are the same kernel
+// with other TMA boxes and shared-memory descriptors (template XK, WMN).
 //
 // Design (GB300, sm_103a):
 //   * persistent CTAs, one per SM (196 KB of shared memory each), tiles of
 //     128 samples x 256 features taken in order with the feature tiles of a
 //     sample block adjacent (the X block is then read from HBM once);
 //   * warp 0: one thread issues the TMA loads (cp.async.bulk.tensor, 128-byte
-//     swizzle) of each K step, 64 deep, into a 4-stage ring: two 64 x 64
-//     boxes of X (samples contiguous: the MMA's A operand, MN-major) and one
-//     64 x 256 box of W (k contiguous: the B operand, K-major);
+//     swizzle) of each K step, 64 deep, into a 4-stage ring of 48 KB: the
+//     128 x 64 tile of X (the MMA's A operand: two 64-sample boxes when the
+//     samples are contiguous, one box of k rows otherwise) and the 256 x 64
+//     tile of W (the B operand: one box of k rows, or four 64-feature boxes);
 //   * warp 1: allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //     and one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 out,
 //     M = 128, N = 256, K = 16), committing each stage back to the loader
@@ -57,10 +62,14 @@ constexpr int SMEM_BYTES = 1024 + TSTAGES * STAGE_BYTES + 256;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 
 // instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits
-// 4-5 = 1), A and B BF16 (bits 7-9 and 10-12 = 1), A MN-major (bit 15), B
-// K-major (bit 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) |
-                           (uint32_t(TBN >> 3) << 17) | (uint32_t(TBM >> 4) << 24);
+// 4-5 = 1), A and B BF16 (bits 7-9 and 10-12 = 1), A MN-major (bit 15) unless
+// X is given k-contiguous, B MN-major (bit 16) when W is given n-contiguous,
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28
+template <bool XK, bool WMN>
+constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (XK ? 0u : (1u << 15)) | (WMN ? (1u << 16) : 0u) |
+         (uint32_t(TBN >> 3) << 17) | (uint32_t(TBM >> 4) << 24);
+}
 
 __device__ int g_tc_error = 0;
 
@@ -91,12 +100,13 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\n"
       "setp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -180,7 +190,9 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs& g, const uint32_t
   }
 }
 
-template <int FL>
+// XK: X given as [m][k] (k contiguous; the weight-gradient products) instead
+// of [k][m].  WMN: W given as [k][n] (n contiguous; W^T dY) instead of [n][k].
+template <int FL, bool XK, bool WMN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
                const GemmArgs g) {
@@ -247,9 +259,22 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
           }
           const uint32_t xs = base + s * STAGE_BYTES, ws = xs + X_BYTES;
           mbar_arrive_expect_tx(full(s), STAGE_BYTES);
-          tma_load_2d(xs, &tmX, full(s), mt * TBM, kb * TBK);
-          tma_load_2d(xs + X_BOX, &tmX, full(s), mt * TBM + 64, kb * TBK);
-          tma_load_2d(ws, &tmW, full(s), kb * TBK, nt * TBN);
+          if (XK) {
+            // one 128-sample x 64-k box, rows of k
+            tma_load_2d(xs, &tmX, full(s), kb * TBK, mt * TBM);
+          } else {
+            // two 64-sample x 64-k boxes, rows of samples
+            tma_load_2d(xs, &tmX, full(s), mt * TBM, kb * TBK);
+            tma_load_2d(xs + X_BOX, &tmX, full(s), mt * TBM + 64, kb * TBK);
+          }
+          if (WMN) {
+            // four 64-feature x 64-k boxes, rows of features
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4)
+              tma_load_2d(ws + q4 * X_BOX, &tmW, full(s), nt * TBN + 64 * q4, kb * TBK);
+          } else {
+            tma_load_2d(ws, &tmW, full(s), kb * TBK, nt * TBN);
+          }
           armed[s] = (int)ph;
           if (++s == TSTAGES) {
             s = 0;
@@ -288,9 +313,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
           for (int k = 0; k < TBK / 16; ++k) {
             // X: 64-sample blocks 8 KB apart (LBO), 8-row k groups 1 KB apart (SBO);
             // 16 k rows = 2 KB per MMA.  W: 8-row groups 1 KB apart; 16 k = 32 bytes.
-            const uint64_t adesc = smem_desc(xs + k * 2048, X_BOX, 1024);
-            const uint64_t bdesc = smem_desc(ws + k * 32, 16, 1024);
-            tc_mma(d, adesc, bdesc, (kb | k) != 0 ? 1u : 0u);
+            // K-major operands (rows of 64 k): 8-row groups 1 KB apart, 16 k = 32 bytes.
+            const uint64_t adesc = XK ? smem_desc(xs + k * 32, 16, 1024)
+                                      : smem_desc(xs + k * 2048, X_BOX, 1024);
+            const uint64_t bdesc = WMN ? smem_desc(ws + k * 2048, X_BOX, 1024)
+                                       : smem_desc(ws + k * 32, 16, 1024);
+            tc_mma(d, adesc, bdesc, idesc<XK, WMN>(), (kb | k) != 0 ? 1u : 0u);
           }
           tc_commit(empty(s));
           if (++s == TSTAGES) {
@@ -391,38 +419,66 @@ void set_gemm_kernel(int mode) { g_tc_mode.store(mode); }
 int get_gemm_kernel() { return g_tc_mode.load(); }
 
 bool gemm_tc_eligible(int amode, int bmode, const GemmArgs& g) {
-  const auto al = [](const void* p, long long ld) {
-    return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 8 == 0 && ld > 0 &&
+  const auto al = [](const void* p, long long ld, long long inner) {
+    return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 8 == 0 && ld >= inner &&
            ld < (1ll << 36);
   };
-  return g_tc_mode.load() != GEMM_KERNEL_MMA_SYNC && amode == GEMM_A_NK && bmode == GEMM_B_KM &&
-         g.N > 0 && g.M > 0 && g.K > 0 && al(g.A, g.lda) && al(g.B, g.ldb) && g.lda >= g.K &&
-         g.ldb >= g.M && encode_fn() != nullptr;
+  const bool xk = bmode == GEMM_B_MK, wmn = amode == GEMM_A_KN;
+  return g_tc_mode.load() != GEMM_KERNEL_MMA_SYNC && (amode == GEMM_A_NK || wmn) &&
+         (bmode == GEMM_B_KM || xk) && g.N > 0 && g.M > 0 && g.K > 0 &&
+         al(g.A, g.lda, wmn ? g.N : g.K) && al(g.B, g.ldb, xk ? g.K : g.M) &&
+         encode_fn() != nullptr;
 }
 
 namespace {
 
-template <int FL>
+template <int FL, bool XK, bool WMN>
 cudaError_t launch_tc(const CUtensorMap& mx, const CUtensorMap& mw, const GemmArgs& g, int grid,
                       cudaStream_t s) {
   static PerDeviceOnce attr;  // per instance: the attribute is per device and kernel
   const int st = attr.run([](int* d) { return cudaGetDevice(d); },
                           [] {
                             return cudaFuncSetAttribute(
-                                gemm_tc_kernel<FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                SMEM_BYTES);
+                                gemm_tc_kernel<FL, XK, WMN>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
                           });
   if (st != 0) return static_cast<cudaError_t>(st);
-  gemm_tc_kernel<FL><<<grid, TC_THREADS, SMEM_BYTES, s>>>(mx, mw, g);
+  gemm_tc_kernel<FL, XK, WMN><<<grid, TC_THREADS, SMEM_BYTES, s>>>(mx, mw, g);
   return cudaGetLastError();
+}
+
+// the epilogue operand sets each orientation is used with (forward layers,
+// weight gradients, W^T dY masked by the pre-activation, fr_gemm_bf16); any
+// other set takes the run-time-tested epilogue
+template <bool XK, bool WMN>
+cudaError_t dispatch_tc(int fl, const CUtensorMap& mx, const CUtensorMap& mw, const GemmArgs& g,
+                        int grid, cudaStream_t s) {
+  if (fl == EP_C) return launch_tc<EP_C, XK, WMN>(mx, mw, g, grid, s);
+  if (!XK && !WMN) {
+    switch (fl) {
+      case EP_BIAS | EP_C | EP_CB | EP_RELU:
+        return launch_tc<EP_BIAS | EP_C | EP_CB | EP_RELU, XK, WMN>(mx, mw, g, grid, s);
+      case EP_BIAS | EP_CB | EP_RELU:
+        return launch_tc<EP_BIAS | EP_CB | EP_RELU, XK, WMN>(mx, mw, g, grid, s);
+      case EP_BIAS | EP_C: return launch_tc<EP_BIAS | EP_C, XK, WMN>(mx, mw, g, grid, s);
+      case EP_BIAS | EP_C | EP_RSCALE:
+        return launch_tc<EP_BIAS | EP_C | EP_RSCALE, XK, WMN>(mx, mw, g, grid, s);
+      default: break;
+    }
+  }
+  if (!XK && WMN && fl == (EP_MASK | EP_C | EP_CB))
+    return launch_tc<EP_MASK | EP_C | EP_CB, XK, WMN>(mx, mw, g, grid, s);
+  return launch_tc<EP_ANY, XK, WMN>(mx, mw, g, grid, s);
 }
 
 }  // namespace
 
-cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t s) {
+cudaError_t launch_gemm_tc(int amode, int bmode, const GemmArgs& g, cudaStream_t s) {
+  const bool xk = bmode == GEMM_B_MK, wmn = amode == GEMM_A_KN;
   CUtensorMap mx, mw;
-  if (!make_map(&mx, g.B, g.M, g.K, g.ldb, TBK) || !make_map(&mw, g.A, g.K, g.N, g.lda, TBN))
-    return cudaErrorInvalidValue;
+  const bool okx = xk ? make_map(&mx, g.B, g.K, g.M, g.ldb, TBM) : make_map(&mx, g.B, g.M, g.K, g.ldb, TBK);
+  const bool okw = wmn ? make_map(&mw, g.A, g.N, g.K, g.lda, TBK) : make_map(&mw, g.A, g.K, g.N, g.lda, TBN);
+  if (!okx || !okw) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -433,16 +489,10 @@ cudaError_t launch_gemm_tc(const GemmArgs& g, cudaStream_t s) {
   const int fl = (g.bias ? EP_BIAS : 0) | (g.mask ? EP_MASK : 0) | (g.row_scale ? EP_RSCALE : 0) |
                  (g.C ? EP_C : 0) | (g.C && g.accumulate ? EP_ACC : 0) | (g.Cb ? EP_CB : 0) |
                  (g.Cb && g.relu ? EP_RELU : 0);
-  // the combinations of the network's forward pass and of fr_gemm_bf16
-  switch (fl) {
-    case EP_C: return launch_tc<EP_C>(mx, mw, g, grid, s);
-    case EP_BIAS | EP_C | EP_CB | EP_RELU:
-      return launch_tc<EP_BIAS | EP_C | EP_CB | EP_RELU>(mx, mw, g, grid, s);
-    case EP_BIAS | EP_CB | EP_RELU: return launch_tc<EP_BIAS | EP_CB | EP_RELU>(mx, mw, g, grid, s);
-    case EP_BIAS | EP_C: return launch_tc<EP_BIAS | EP_C>(mx, mw, g, grid, s);
-    case EP_BIAS | EP_C | EP_RSCALE: return launch_tc<EP_BIAS | EP_C | EP_RSCALE>(mx, mw, g, grid, s);
-    default: return launch_tc<EP_ANY>(mx, mw, g, grid, s);
-  }
+  if (!xk && !wmn) return dispatch_tc<false, false>(fl, mx, mw, g, grid, s);
+  if (xk && !wmn) return dispatch_tc<true, false>(fl, mx, mw, g, grid, s);
+  if (!xk && wmn) return dispatch_tc<false, true>(fl, mx, mw, g, grid, s);
+  return dispatch_tc<true, true>(fl, mx, mw, g, grid, s);
 }
 
 int gemm_tc_status() {

@@ -542,7 +542,7 @@ int blocks_for(long long n) {
 }  // namespace
 
 cudaError_t launch_gemm(int amode, int bmode, const GemmArgs& g, cudaStream_t s) {
-  if (gemm_tc_eligible(amode, bmode, g)) return launch_gemm_tc(g, s);
+  if (gemm_tc_eligible(amode, bmode, g)) return launch_gemm_tc(amode, bmode, g, s);
   const auto a16 = [](const void* p, long long ld) {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 8 == 0;
   };

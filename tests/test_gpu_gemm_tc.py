@@ -1,7 +1,7 @@
 """The fifth-generation tensor-core GEMM (tcgen05.mma, TMEM accumulators, TMA
-operand tiles) of the network's forward orientation, C[N x M] = A[N x K] .
-B[K x M], against numpy on the BF16-rounded operands and against the
-warp-level mma.sync kernels, through the C ABI.
+operand tiles) of the network, C[N x M] = A[N x K] . B[K x M] with either
+operand stored either way, against numpy on the BF16-rounded operands and
+against the warp-level mma.sync kernels, through the C ABI.
 
 Both kernels multiply BF16 values exactly and accumulate in FP32, so the
 error bound is a few FP32 unit round-offs of the summed magnitudes:
@@ -112,3 +112,49 @@ def test_unaligned_operands_take_mma_sync(abi):
 def test_set_kernel_rejects_unknown(abi):
     with pytest.raises(abi.FrError):
         abi.fr_gemm_set_kernel(7)
+
+
+ORIENT_SHAPES = [
+    # (N, M, K): one tile; ragged; the weight gradients of the network
+    # (dW3: 1625 x 256 over 4500 samples, dW1: 256 x 4875) and W^T dY
+    # (256 x 4500 over 1625 features)
+    (256, 128, 64),
+    (70, 130, 100),
+    (1625, 256, 4500),
+    (256, 4875, 4500),
+    (256, 4500, 1625),
+]
+
+
+def _pad8(n):
+    return (n + 7) // 8 * 8
+
+
+@pytest.mark.parametrize("amode,bmode", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("N,M,K", ORIENT_SHAPES)
+def test_tcgen05_gemm_every_orientation(abi, amode, bmode, N, M, K):
+    """amode 0: A[n][k], 1: A[k][n]; bmode 0: B[k][m], 1: B[m][k] (the
+    backward products read the operands the other way), with 16-byte row
+    pitches so that the tensor-memory kernel serves all four."""
+    rng = np.random.default_rng(N + 3 * M + 7 * K + amode * 2 + bmode)
+    A = torch.from_numpy(rng.normal(size=(N, K)).astype(np.float32)).to(torch.bfloat16)
+    B = torch.from_numpy(rng.normal(size=(K, M)).astype(np.float32)).to(torch.bfloat16)
+    A64 = A.float().numpy().astype(np.float64)
+    B64 = B.float().numpy().astype(np.float64)
+    As = A if amode == 0 else A.t()
+    Bs = B if bmode == 0 else B.t()
+    lda, ldb = _pad8(As.shape[1]) + 8, _pad8(Bs.shape[1]) + 8
+    Ad = torch.zeros((As.shape[0], lda), dtype=torch.bfloat16)
+    Ad[:, :As.shape[1]] = As
+    Bd = torch.zeros((Bs.shape[0], ldb), dtype=torch.bfloat16)
+    Bd[:, :Bs.shape[1]] = Bs
+    Ad, Bd = Ad.cuda(), Bd.cuda()
+    abi.fr_gemm_set_kernel(abi.FR_GEMM_AUTO)
+    C = torch.full((N, M), float("nan"), dtype=torch.float32, device="cuda")
+    abi.fr_gemm_bf16(amode, bmode, N, M, K, Ad, lda, Bd, ldb, C, M)
+    abi.fr_gemm_check()
+    C = C.cpu().numpy().astype(np.float64)
+    ref, mag = A64 @ B64, np.abs(A64) @ np.abs(B64)
+    assert np.all(np.isfinite(C))
+    bad = np.abs(C - ref) > 1e-5 * mag + 1e-30
+    assert not bad.any(), (int(bad.sum()), float(np.max(np.abs(C - ref) / (mag + 1e-30))))
