@@ -80,24 +80,9 @@ __device__ __forceinline__ T trace_dot(const T (&x)[M], const T* ell) {
   return acc;
 }
 
-// Normal flux F_a in slot order from the slot values u[0..2D].
-template <int D, typename T>
-__device__ __forceinline__ void slot_flux(const T (&u)[1 + 2 * D], int a, T zeta, T nu,
-                                          T inv_t, T (&f)[1 + 2 * D]) {
-  const T va = u[1 + a];
-  f[0] = rn_mul(zeta, va);
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    // V_i V_a + P delta_ia - nu d(V_i)/dx_a
-    T t = rn_mul(nu, u[1 + D + i]);
-    t = (i == a) ? rn_sub(u[0], t) : -t;
-    f[1 + i] = rn_fma(u[1 + i], va, t);
-    f[1 + D + i] = -rn_mul(u[1 + i], inv_t);
-  }
-}
-
-// Slot s of the normal flux F_a at point t of a line held as u[slot][point]
-// (same arithmetic as slot_flux, one slot at a time).
+// Slot s of the normal flux F_a at point t of a line held as u[slot][point]:
+// slot 0 zeta V_a; slot 1+i V_i V_a + P delta_ia - nu d(V_i)/dx_a; slot
+// 1+D+i -V_i / T.
 template <int D, int M, typename T>
 __device__ __forceinline__ T point_flux(const T (&u)[1 + 2 * D][M], int t, int s, int a, T zeta,
                                         T nu, T inv_t) {
@@ -115,21 +100,33 @@ __device__ __forceinline__ T point_flux(const T (&u)[1 + 2 * D][M], int t, int s
 // Common interface flux on a face with normal +e_a, uL on the low side:
 // mean flux plus Rusanov dissipation (s/2)(uR - uL) on P and V, where
 // s = max(|V_a| + sqrt(V_a^2 + zeta)) over both sides (Sec. 5).
+//  * |V| + sqrt(V^2 + zeta), each operation rounded to nearest, does not
+//    decrease as |V| grows, so the larger of the two sides' speeds is the
+//    speed of the larger |V_a|, bit for bit: one square root per face point.
+//  * The P and auxiliary slots are linear in the state (zeta V_a, -V_i / T),
+//    so their mean flux is formed from the sum of the two states.
+// Both elements of a face call this with the same (uL, uR) and obtain the
+// same bits.
 template <int D, typename T>
 __device__ __forceinline__ void common_flux(const T (&uL)[1 + 2 * D], const T (&uR)[1 + 2 * D],
                                             int a, T zeta, T nu, T inv_t,
                                             T (&fi)[1 + 2 * D]) {
-  T fL[1 + 2 * D], fR[1 + 2 * D];
-  slot_flux<D>(uL, a, zeta, nu, inv_t, fL);
-  slot_flux<D>(uR, a, zeta, nu, inv_t, fR);
   const T vl = uL[1 + a], vr = uR[1 + a];
-  const T sl = rn_add(vabs(vl), rn_sqrt(rn_fma(vl, vl, zeta)));
-  const T sr = rn_add(vabs(vr), rn_sqrt(rn_fma(vr, vr, zeta)));
-  const T hs = rn_mul(T(0.5), vmax(sl, sr));
+  const T vm = vmax(vabs(vl), vabs(vr));
+  const T hs = rn_mul(T(0.5), rn_add(vm, rn_sqrt(rn_fma(vm, vm, zeta))));
+  const T hz = rn_mul(T(0.5), zeta);
+  const T hit = rn_mul(T(-0.5), inv_t);
+  fi[0] = rn_fma(-hs, rn_sub(uR[0], uL[0]), rn_mul(hz, rn_add(vl, vr)));
 #pragma unroll
-  for (int s = 0; s < 1 + 2 * D; ++s) {
-    const T mean = rn_mul(T(0.5), rn_add(fL[s], fR[s]));
-    fi[s] = (s <= D) ? rn_fma(-hs, rn_sub(uR[s], uL[s]), mean) : mean;
+  for (int i = 0; i < D; ++i) {
+    // V_i V_a + P delta_ia - nu d(V_i)/dx_a on each side, then the mean
+    T tl = rn_mul(nu, uL[1 + D + i]);
+    T tr = rn_mul(nu, uR[1 + D + i]);
+    tl = (i == a) ? rn_sub(uL[0], tl) : -tl;
+    tr = (i == a) ? rn_sub(uR[0], tr) : -tr;
+    const T mean = rn_mul(T(0.5), rn_add(rn_fma(uL[1 + i], vl, tl), rn_fma(uR[1 + i], vr, tr)));
+    fi[1 + i] = rn_fma(-hs, rn_sub(uR[1 + i], uL[1 + i]), mean);
+    fi[1 + D + i] = rn_mul(hit, rn_add(uL[1 + i], uR[1 + i]));
   }
 }
 
