@@ -20,6 +20,8 @@ timestep  Classical RK4 pseudo-time step, BDF2 dual time stepping and the
           FP64 velocity residual (Sec. 5).
 mlp       Per-element MLP forward/backward/Adam for the learned initial guess
           (no counterpart in the paper).
+pmg       P-multigrid (full approximation scheme over the orders p .. 0) and
+          Anderson mixing of its cycles for the pseudo-time solve (Sec. 5).
 
 Parity status: every module's docstring lists what pins it (closed forms,
 textbook operators derived independently with sympy, invariants, brute
