@@ -692,6 +692,8 @@ def run_dual(args):
     cap_samples = per_step * n_collect
     abi.fr_dual_init(A.c, A.U)
     net = abi.fr_mlp_create(A.c, args.dual_hidden, cap_samples, seed=2021)
+    if args.dual_mlp_degree >= 0:
+        abi.fr_mlp_set_output_degree(net, args.dual_mlp_degree)
     log = {"A": [], "B": []}
 
     def step(S, name, k, guess, cap, mlp=None):
@@ -751,7 +753,8 @@ def run_dual(args):
             "max_iter_held_steps": args.dual_held_iters,
             "mlp": {"hidden": args.dual_hidden, "samples": cap_samples, "validation": n_val,
                     "epochs": args.dual_epochs, "best_epochs": best[1], "lr": args.dual_lr,
-                    "weight_decay": args.dual_wd, "train_s": t_train, "loss_first": loss0,
+                    "weight_decay": args.dual_wd, "output_degree": args.dual_mlp_degree,
+                    "train_s": t_train, "loss_first": loss0,
                     "curve": curve}}),
         "plain_wall_s": wa, "learned_wall_s": wb, "speedup": wa / wb,
         "held_out_steps": n_held, "max_velocity_difference": dv,
@@ -1079,6 +1082,8 @@ def main():
                     help="fine-iteration equivalents of one cycle, to turn the iteration "
                          "caps into cycle caps")
     ap.add_argument("--dual-wd", type=float, default=1e-2, help="weight decay of the network")
+    ap.add_argument("--dual-mlp-degree", type=int, default=-1,
+                    help="project the learned corrections onto degree <= q per element (-1: off)")
     ap.add_argument("--dual-val-every", type=int, default=25,
                     help="epochs between validation-loss checks")
     ap.add_argument("--dual-steps", type=int, default=200,

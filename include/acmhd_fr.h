@@ -437,6 +437,19 @@ int fr_mlp_train_step(fr_mlp* mlp, double lr, double* loss, void* stream);
  * in fr_last_error) for a missing, corrupt or foreign file, or a network of
  * another discretization (dimension, order or variable count). */
 int fr_mlp_save(const fr_mlp* mlp, const char* path);
+
+/* Smoothing of the learned correction (no counterpart in the paper): with
+ * degree q >= 0, every correction the network learns from (the targets that
+ * fr_mlp_collect gathers from then on) and every correction it predicts is
+ * projected, per element and variable, onto the polynomials of degree <= q
+ * in each direction (the L2 projection on the element's Gauss-Legendre
+ * points, applied along each axis).  The network then neither learns nor
+ * adds element-scale detail, which the pseudo-time residual penalises, and
+ * keeps the smooth part of the correction, which the extrapolated guess
+ * carries forward.  degree -1 (the default) turns it off; q = order is the
+ * identity.  FR_EINVAL outside [-1, order].  The setting is not saved by
+ * fr_mlp_save. */
+int fr_mlp_set_output_degree(fr_mlp* mlp, int degree);
 int fr_mlp_load(fr_ctx* ctx, const char* path, int capacity, fr_mlp** out);
 
 /* The tensor-core GEMM of the MLP as a utility: C[N x M] = A . B in FP32

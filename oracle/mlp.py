@@ -132,3 +132,31 @@ def blend_weight(r0, r1):
     if dd == 0.0:
         return 0.0
     return float(np.clip(-np.sum(np.asarray(r0) * d) / dd, 0.0, 1.0))
+
+
+def degree_projector(order, q):
+    """1-D L2 projection onto polynomials of degree <= q, as an (m x m)
+    matrix acting on values at the m = order + 1 Gauss-Legendre points:
+    P[i, k] = sum_{n <= q} phi_n(x_i) phi_n(x_k) w_k with the orthonormal
+    Legendre polynomials phi_n = sqrt((2n + 1) / 2) P_n (the m-point rule is
+    exact for the products, degree <= 2 order).  No counterpart in the paper:
+    it smooths the learned correction of the initial guess."""
+    from oracle.ops1d import gauss_legendre, legendre
+    x, w = gauss_legendre(order + 1)
+    phi = np.stack([np.sqrt((2 * n + 1) / 2.0) * legendre(n, x)[0] for n in range(q + 1)],
+                   axis=1)
+    return phi @ (phi.T * w[None, :])
+
+
+def project_degree(Y, order, dim, q):
+    """Per-element, per-variable tensor-product projection of Y ((n_v npts) x
+    B, point index i + m j + m^2 k) onto degree <= q along every axis."""
+    m = order + 1
+    P = degree_projector(order, q)
+    B = Y.shape[1]
+    Z = np.asarray(Y, dtype=np.float64).reshape((-1,) + (m,) * dim + (B,))
+    # axes of Z: (v, [k,] j, i, B); the x axis (i) is the last spatial one
+    for ax in range(1, dim + 1):
+        Z = np.moveaxis(np.tensordot(P, Z, axes=([1], [ax])), 0, ax)
+    return Z.reshape(Y.shape)
+

@@ -30,7 +30,8 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_layout", "fr_rhs", "fr_set_schedule", 
            "fr_mlp_train_step", "fr_mlp_save", "fr_mlp_load", "fr_fma_probe",
            "fr_pmg_create", "fr_pmg_destroy", "fr_pmg_set_cycle", "fr_pmg_set_dtau",
            "fr_pmg_solve", "fr_pmg_set_anderson", "fr_mlp_set_training",
-           "fr_mlp_validation_loss", "fr_gemm_set_kernel", "fr_gemm_check"]
+           "fr_mlp_validation_loss", "fr_gemm_set_kernel", "fr_gemm_check",
+           "fr_mlp_set_output_degree"]
 
 
 class fr_mesh(ctypes.Structure):
@@ -119,6 +120,7 @@ def _lib():
         lib.fr_gemm_bf16.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.c_longlong, vp,
                                      ctypes.c_longlong, vp, ctypes.c_longlong, vp]
         lib.fr_gemm_set_kernel.argtypes = [i32]
+        lib.fr_mlp_set_output_degree.argtypes = [vp, i32]
         lib.fr_gemm_check.argtypes = [vp]
         lib.fr_strerror.argtypes = [i32]
         lib.fr_strerror.restype = ctypes.c_char_p
@@ -448,6 +450,11 @@ def fr_gemm_bf16(amode, bmode, N, M, K, A, lda, B, ldb, C, ldc, stream=None):
     _check(_lib().fr_gemm_bf16(int(amode), int(bmode), int(N), int(M), int(K), _ptr(A), int(lda),
                                _ptr(B), int(ldb), _ptr(C), int(ldc), _stream(stream)),
            "fr_gemm_bf16")
+
+
+def fr_mlp_set_output_degree(mlp, degree):
+    _check(_lib().fr_mlp_set_output_degree(ctypes.c_void_p(mlp), int(degree)),
+           "fr_mlp_set_output_degree")
 
 
 FR_GEMM_AUTO, FR_GEMM_MMA_SYNC = 0, 1

@@ -31,6 +31,11 @@ struct Ops1D {
 // Builds the operators; correction is FR_CORR_DG or FR_CORR_G2.
 bool build_ops1d(int order, int correction, Ops1D* out);
 
+// 1-D L2 projection onto polynomials of degree <= q on the GL points of o:
+// P[i][k] = sum_{n <= q} phi_n(x_i) phi_n(x_k) w_k, phi_n the orthonormal
+// Legendre polynomials (smoothing of the learned initial guess's correction).
+void degree_projector(const Ops1D& o, int q, double (*P)[kMaxM]);
+
 // Everything a kernel needs, passed by value (lands in the constant bank).
 template <typename T>
 struct FrConst {

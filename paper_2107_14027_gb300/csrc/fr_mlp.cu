@@ -52,6 +52,8 @@ struct fr_mlp {
   float* Yc;             // [NO x stride] scaled corrections
   __nv_bfloat16* w1p;    // [H x Kp] BF16 W1 with rows padded to a multiple of 8
   int Kp;                //   values (16 bytes), the tensor-memory GEMM's TMA pitch
+  int out_degree;        // corrections projected onto degree <= out_degree (-1: off)
+  acmhd::LineProj proj;  //   the 1-D projector of that degree
 };
 
 namespace {
@@ -245,6 +247,7 @@ int fr_mlp_create(fr_ctx* c, int hidden, int capacity, unsigned long long seed, 
   fr_mlp* q = new (std::nothrow) fr_mlp;
   if (!q) return FR_ENOMEM;
   std::memset(q, 0, sizeof(*q));
+  q->out_degree = -1;
   q->ctx = c;
   q->NO = c->nv * c->npts;
   q->K = 3 * q->NO;
@@ -437,6 +440,11 @@ int fr_mlp_collect(fr_mlp* q, int count, unsigned long long seed, int* elems_out
     if (!st) st = st_of(acmhd::launch_gather_targets(h, q->elems + q->n, count, q->Ts + q->n, ld, s),
                         "mlp targets");
   }
+  // smoothed targets: the corrections projected onto degree <= out_degree
+  if (st == FR_OK && q->out_degree >= 0)
+    st = st_of(acmhd::launch_project_lines(q->Ts + q->n, ld, count, c->nv, c->m, c->dim, q->proj,
+                                           s),
+               "mlp targets");
   if (st == FR_OK) st = st_of(cudaStreamSynchronize(s), "mlp collect");
   if (st == FR_OK) q->n += count;
   return st;
@@ -551,6 +559,10 @@ int fr_mlp_predict_for(fr_mlp* q, fr_ctx* c, void* U, double* V, void* stream) {
   // hidden layers keep only their BF16 activations; the output is scaled
   if ((st = forward(q, q->Xi, ld, (int)ld, nullptr, q->Hi1, nullptr, q->Hi2, q->Yc, q->out_scale, s)))
     return st;
+  if (q->out_degree >= 0 &&
+      (st = st_of(acmhd::launch_project_lines(q->Yc, ld, c->ne, c->nv, c->m, c->dim, q->proj, s),
+                  "mlp smoothing")))
+    return st;
   if (c->precision == FR_F32)
     st = st_of(acmhd::launch_apply_guess(hist_view<float>(c, lev), q->Yc, ld, static_cast<float*>(U), V, s),
                "mlp guess");
@@ -558,6 +570,19 @@ int fr_mlp_predict_for(fr_mlp* q, fr_ctx* c, void* U, double* V, void* stream) {
     st = st_of(acmhd::launch_apply_guess(hist_view<double>(c, lev), q->Yc, ld, static_cast<double*>(U), V, s),
                "mlp guess");
   return st;
+}
+
+int fr_mlp_set_output_degree(fr_mlp* q, int degree) {
+  if (!q || degree < -1 || degree > q->ctx->order) return FR_EINVAL;
+  q->out_degree = degree;
+  if (degree >= 0) {
+    double P[acmhd::kMaxM][acmhd::kMaxM];
+    acmhd::degree_projector(q->ctx->ops, degree, P);
+    for (int i = 0; i < acmhd::kMaxM; ++i)
+      for (int k = 0; k < acmhd::kMaxM; ++k)
+        q->proj.P[i][k] = (i < q->ctx->m && k < q->ctx->m) ? (float)P[i][k] : 0.0f;
+  }
+  return FR_OK;
 }
 
 int fr_mlp_train_step(fr_mlp* q, double lr, double* loss, void* stream) {

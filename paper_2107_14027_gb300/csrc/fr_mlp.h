@@ -86,4 +86,13 @@ cudaError_t launch_adam(size_t n, float* p, const float* g, float* m, float* v, 
                         cudaStream_t s);
 cudaError_t launch_to_bf16(size_t n, const float* x, __nv_bfloat16* y, cudaStream_t s);
 
+// Per column and variable of Y[(v npts + pt) * ld + j] (npts = m^dim points,
+// pt = i + m j + m^2 k), the tensor-product projection with the 1-D matrix P
+// along every axis, in place (columns [0, ncols)).
+struct LineProj {
+  float P[kMaxM][kMaxM];
+};
+cudaError_t launch_project_lines(float* Y, long long ld, int ncols, int nv, int m, int dim,
+                                 const LineProj& p, cudaStream_t s);
+
 }  // namespace acmhd

@@ -51,6 +51,21 @@ double corr_left_d(int correction, int m, double x) {
 
 }  // namespace
 
+void degree_projector(const Ops1D& o, int q, double (*P)[kMaxM]) {
+  // P[i][k] = sum_{n <= q} phi_n(x_i) phi_n(x_k) w_k, phi_n = sqrt((2n+1)/2) P_n
+  for (int i = 0; i < o.m; ++i)
+    for (int k = 0; k < o.m; ++k) {
+      double acc = 0.0;
+      for (int n = 0; n <= q; ++n) {
+        double pi, pk, d;
+        legendre_pd(n, o.xi[i], &pi, &d);
+        legendre_pd(n, o.xi[k], &pk, &d);
+        acc += (2.0 * n + 1.0) / 2.0 * pi * pk * o.w[k];
+      }
+      P[i][k] = acc;
+    }
+}
+
 bool build_ops1d(int order, int correction, Ops1D* o) {
   const int m = order + 1;
   if (m < 2 || m > kMaxM) return false;

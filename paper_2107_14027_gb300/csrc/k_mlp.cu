@@ -534,6 +534,35 @@ pad_rows_kernel(const __nv_bfloat16* __restrict__ src, int rows, int cols,
   }
 }
 
+// One line of M points along `axis` of one variable of one column per thread
+// (columns fastest: every access is a contiguous row segment), in place.
+template <int M>
+__global__ void __launch_bounds__(256)
+project_lines_kernel(float* __restrict__ Y, long long ld, int ncols, int nv, int dim, int axis,
+                     const LineProj p) {
+  const int npts = dim == 3 ? M * M * M : M * M;
+  const int nl = npts / M;
+  const int ma = axis == 0 ? 1 : (axis == 1 ? M : M * M);
+  const long long total = (long long)ncols * nv * nl;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long j = idx % ncols;
+    const long long rest = idx / ncols;
+    const int l = (int)(rest % nl), v = (int)(rest / nl);
+    const int base = v * npts + (l % ma) + ma * M * (l / ma);
+    float x[M];
+#pragma unroll
+    for (int t = 0; t < M; ++t) x[t] = Y[(long long)(base + ma * t) * ld + j];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      float y = 0.0f;
+#pragma unroll
+      for (int k = 0; k < M; ++k) y = fmaf(p.P[i][k], x[k], y);
+      Y[(long long)(base + ma * i) * ld + j] = y;
+    }
+  }
+}
+
 int blocks_for(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
@@ -652,6 +681,27 @@ cudaError_t launch_adam(size_t n, float* p, const float* g, float* m, float* v, 
   adam_kernel<<<blocks_for((long long)n), 256, 0, s>>>(n, p, g, m, v, pb, lr, b1, b2, eps, c1, c2,
                                                        wd);
   return cudaGetLastError();
+}
+
+cudaError_t launch_project_lines(float* Y, long long ld, int ncols, int nv, int m, int dim,
+                                 const LineProj& p, cudaStream_t s) {
+  if (ncols < 1) return cudaSuccess;
+  const long long total = (long long)ncols * nv * (dim == 3 ? m * m : m);
+  for (int axis = 0; axis < dim; ++axis) {
+    switch (m) {
+#define ACMHD_PROJ(MM)                                                                     \
+  case MM:                                                                                 \
+    project_lines_kernel<MM><<<blocks_for(total), 256, 0, s>>>(Y, ld, ncols, nv, dim, axis, \
+                                                               p);                         \
+    break;
+      ACMHD_PROJ(2) ACMHD_PROJ(3) ACMHD_PROJ(4) ACMHD_PROJ(5) ACMHD_PROJ(6) ACMHD_PROJ(7)
+#undef ACMHD_PROJ
+      default: return cudaErrorInvalidValue;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_to_bf16(size_t n, const float* x, __nv_bfloat16* y, cudaStream_t s) {

@@ -539,3 +539,53 @@ def test_learned_guess_gain_on_the_dual_time_workload_24cube(abi):
         for c, c64, *_ in solvers:
             abi.fr_destroy(c)
             abi.fr_destroy(c64)
+
+
+@pytest.mark.parametrize("n,order,q", [((6, 5), 2, 1), ((4, 4, 3), 3, 1), ((4, 3, 3), 4, 2)])
+def test_output_degree_projection_matches_oracle(abi, n, order, q):
+    """fr_mlp_set_output_degree(q): the collected targets and the predicted
+    corrections are the oracle's, projected per element onto degree <= q
+    (oracle.mlp.project_degree, pinned on the CPU)."""
+    d = len(n)
+    ctx, Ud, levels, nv = _history_case(abi, n=n, order=order, dtau=1e-2 if d == 2 else 2e-3)
+    S, H = 48, 32
+    net = abi.fr_mlp_create(ctx, H, S, seed=5)
+    try:
+        with pytest.raises(abi.FrError):
+            abi.fr_mlp_set_output_degree(net, order + 1)
+        abi.fr_mlp_set_output_degree(net, q)
+        K, Hh, NO, _, npar = abi.fr_mlp_info(net)
+        el = abi.fr_mlp_collect(net, S, seed=9)
+        Un, Unm1, Unm2, Unp1 = levels[-2], levels[-3], levels[-4], levels[-1]
+        Tr = abi.fr_mlp_params(net, 4, count=NO * S).reshape(NO, S).astype(np.float64)
+        raw = (Unp1 - omlp.extrapolate(Un, Unm1, Unm2))[:, :, el].reshape(NO, S)
+        ref = omlp.project_degree(raw, order, d, q)
+        scale = np.abs(raw).max()
+        assert np.abs(Tr - ref).max() <= 1e-5 * scale, np.abs(Tr - ref).max() / scale
+        abi.fr_mlp_train(net, 2, 1e-3)
+        scales = abi.fr_mlp_params(net, 2, count=4 * nv)
+        s0, s1, s2 = scales[:nv], scales[nv:2 * nv], scales[2 * nv:3 * nv]
+        t = scales[3 * nv:].astype(np.float64)
+        sizes = [(H, K), (H, H), (NO, H)]
+        params = _unflatten(abi.fr_mlp_params(net, 0, count=npar), sizes)
+        Ug = abi.new_state(ctx, 64)
+        Vg = abi.new_velocity(ctx, d, order)
+        abi.fr_mlp_predict(net, Ug, Vg)
+        torch.cuda.synchronize()
+        G = abi.unpack_state(ctx, Ug, nv)
+        a, b_, c = levels[-1], levels[-2], levels[-3]
+        ne = a.shape[2]
+        Xall = omlp.features(a, b_, c, (s0, s1, s2), np.arange(ne))
+        Yall, (_, _, _, _, H2a) = omlp.forward(params, Xall)
+        Yp = omlp.project_degree(Yall, order, d, q)
+        corr_gpu = (G - omlp.extrapolate(a, b_, c)).reshape(NO, ne)
+        corr_ref = t.repeat(NO // nv)[:, None] * Yp
+        mag = (np.abs(params[2][0]) @ np.abs(H2a) + np.abs(params[2][1])[:, None])
+        mag = t.repeat(NO // nv)[:, None] * mag
+        assert np.linalg.norm(corr_gpu - corr_ref) < BF16_TOL * np.linalg.norm(mag)
+        # the predicted correction has no content above degree q
+        np.testing.assert_allclose(omlp.project_degree(corr_gpu, order, d, q), corr_gpu,
+                                   rtol=0, atol=1e-5 * np.abs(corr_gpu).max())
+    finally:
+        abi.fr_mlp_destroy(net)
+        abi.fr_destroy(ctx)

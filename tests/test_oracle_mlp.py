@@ -99,7 +99,7 @@ def test_adamw_decay_with_zero_gradient():
     params = [(rng.normal(size=(4, 3)), rng.normal(size=4)), (rng.normal(size=(2, 4)),
                                                               rng.normal(size=2))]
     zeros = [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
-    opt = omlp.Adam(params, lr=1e-2, weight_decay=0.5)
+    opt = mlp.Adam(params, lr=1e-2, weight_decay=0.5)
     new = opt.step(params, zeros)
     for (W, b), (W1, b1) in zip(params, new):
         np.testing.assert_allclose(W1, (1 - 1e-2 * 0.5) * W, rtol=1e-15)
@@ -115,8 +115,61 @@ def test_blend_weight_minimises_a_linear_residual_on_the_segment():
     for trial in range(20):
         u0, u1 = rng.normal(size=12), rng.normal(size=12)
         r0, r1 = A @ u0 - f, A @ u1 - f
-        alpha = omlp.blend_weight(r0, r1)
+        alpha = mlp.blend_weight(r0, r1)
         grid = np.linspace(0.0, 1.0, 20001)
         res = [np.linalg.norm(A @ ((1 - a) * u0 + a * u1) - f) for a in grid]
         best = grid[int(np.argmin(res))]
         assert abs(alpha - best) <= 1e-4, (alpha, best)
+
+
+# --- the degree projection of the learned correction (smoothing) -----------
+
+@pytest.mark.parametrize("order,q", [(1, 0), (2, 1), (3, 1), (4, 2), (4, 0), (6, 3)])
+def test_degree_projection_pins(order, q):
+    """Pinned by what an L2 projection is: polynomials of degree <= q in each
+    direction are reproduced, a Legendre mode of degree q + 1 along any axis
+    is removed, the map is idempotent, and in 1-D it equals weighted least
+    squares on the monomials x^0..x^q (numpy lstsq) with the GL weights."""
+    m = order + 1
+    x, w = np.polynomial.legendre.leggauss(m)
+    P = mlp.degree_projector(order, q)
+    # 1-D: weighted least squares with a monomial basis (independent route)
+    V = np.vander(x, q + 1, increasing=True)
+    sw = np.sqrt(w)[:, None]
+    rng = np.random.default_rng(order * 10 + q)
+    f = rng.normal(size=m)
+    coef, *_ = np.linalg.lstsq(sw * V, sw[:, 0] * f, rcond=None)
+    np.testing.assert_allclose(P @ f, V @ coef, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(P @ P, P, rtol=0, atol=1e-13)
+    # 3-D: tensor-product polynomials of degree <= q are kept
+    gx, gy, gz = np.meshgrid(x, x, x, indexing="ij")        # (i, j, k) = (x, y, z)
+    poly = (1.0 + gx ** q) * (0.5 - gy ** max(q - 1, 0)) * (2.0 + gz)
+    if q == 0:
+        poly = np.full_like(gx, 1.7)
+    Y = np.stack([poly.transpose(2, 1, 0).reshape(-1), 2.0 * poly.transpose(2, 1, 0).reshape(-1)])
+    Y = Y.reshape(-1, 1)                                     # 2 variables, one column
+    np.testing.assert_allclose(mlp.project_degree(Y, order, 3, q), Y, rtol=0, atol=1e-12)
+    # a Legendre mode of degree q + 1 along y alone is removed
+    if q + 1 <= order:
+        Lq = np.polynomial.legendre.legval(gy, [0] * (q + 1) + [1.0])
+        Z = (Lq * (1.0 + gx ** min(q, 1))).transpose(2, 1, 0).reshape(-1, 1)
+        np.testing.assert_allclose(mlp.project_degree(Z, order, 3, q), 0.0, rtol=0, atol=1e-12)
+    # idempotent on random data, also in 2-D
+    R = rng.normal(size=(3 * m ** 2, 4))
+    R1 = mlp.project_degree(R, order, 2, q)
+    np.testing.assert_allclose(mlp.project_degree(R1, order, 2, q), R1, rtol=0, atol=1e-12)
+
+
+def test_degree_projection_catches_a_wrong_axis_order():
+    """Planted mistake: projecting only along one axis (or with the degree
+    taken as q + 1) leaves the degree-(q + 1) mode in place."""
+    order, q = 3, 1
+    m = order + 1
+    x, _ = np.polynomial.legendre.leggauss(m)
+    gx, gy, gz = np.meshgrid(x, x, x, indexing="ij")
+    Z = np.polynomial.legendre.legval(gz, [0, 0, 1.0]).transpose(2, 1, 0).reshape(-1, 1)
+    P = mlp.degree_projector(order, q)
+    only_x = np.tensordot(P, Z.reshape(m, m, m, 1), axes=([1], [2])).transpose(1, 2, 0, 3)
+    assert np.abs(only_x).max() > 0.1
+    assert np.abs(mlp.project_degree(Z, order, 3, q + 1)).max() > 0.1
+    assert np.abs(mlp.project_degree(Z, order, 3, q)).max() < 1e-12
