@@ -768,7 +768,7 @@ def run_dual(args):
 
 def run_dual_steps(args):
     """--dual-steps physical steps of the dual-time workload with the plain
-    extrapolated guess (BASELINE's 200-step run), pseudo-iterations and
+    extrapolated guess (the workload's 200-step run), pseudo-iterations and
     wall-seconds per step logged; for the first --dual-fp64-ref steps an
     FP64-only solver (FP64 RHS, same solver otherwise) runs the same steps
     from the same initial state and the largest velocity difference between
