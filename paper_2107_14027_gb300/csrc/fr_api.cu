@@ -55,6 +55,8 @@ void fill_const_t(const fr_ctx* c, acmhd::FrConst<T>* k) {
   k->n[2] = c->dim == 3 ? c->mesh.n[2] : 1;
   k->ne = c->ne;
   k->stride = static_cast<int>(c->stride);
+  const int E = acmhd::fused_tile_elements(c->dim, c->m, sizeof(T) == 4 ? FR_F32 : FR_F64);
+  k->xcompact = (E > 0 && c->mesh.n[0] % E == 0) ? 1 : 0;
 }
 
 int alloc_zeroed(void** p, size_t bytes, const char* what) {

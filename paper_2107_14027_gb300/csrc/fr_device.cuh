@@ -203,6 +203,16 @@ __device__ __forceinline__ bool x_pair_on_chip(int e_left, int e_right, int E) {
   return e_right == e_left + 1 && (e_right % E) != 0;
 }
 
+// Column of an x-face trace in the trace buffer.  When the rows of elements
+// along x are whole lane groups (n_x a multiple of E), only the first element
+// of a group stores its low x face and only the last its high x face, so the
+// group index serves as the column: the values that neighbouring CTAs read
+// then share sectors instead of each taking a sector of its own.  Otherwise
+// the element index (the layout of the y and z faces).
+__device__ __forceinline__ size_t x_col(int e, int E, int xcompact) {
+  return xcompact ? (size_t)(e / E) : (size_t)e;
+}
+
 }  // namespace acmhd
 
 // Dispatch a runtime (dim, m) pair to a template call FN<D, M>(args...).

@@ -53,6 +53,7 @@ struct FrConst {
   int n[3];        // elements per direction (n[2] = 1 in 2-D)
   int ne;          // number of elements
   int stride;      // elem_stride
+  int xcompact;    // x-face traces at lane-group ends stored by group (x_col)
 };
 
 // most slabs of the host-buffer RHS pipeline (fr_rhs_host).  Measured on

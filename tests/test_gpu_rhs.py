@@ -46,6 +46,9 @@ CASES = [
     ((5, 7), 1), ((5, 7), 2), ((5, 7), 3), ((6, 5), 4), ((5, 7), 5), ((3, 11), 6),
     ((3, 4, 5), 1), ((3, 4, 5), 2), ((3, 4, 5), 3), ((4, 3, 5), 4), ((3, 4, 3), 5), ((3, 2, 5), 6),
     ((9, 8, 7), 3), ((1, 2, 3), 2), ((1, 1, 1), 3), ((2, 1, 1), 4), ((40, 3), 2),
+    # rows along x of whole lane groups: the x-face traces at group ends are
+    # stored by group (every precision's tile size divides these n_x)
+    ((32, 3, 2), 3), ((64, 3), 2), ((16, 3, 2), 4), ((8, 2, 2), 6),
 ]
 
 
