@@ -132,8 +132,8 @@ int fr_rhs(fr_ctx* ctx, const void* U, void* R, void* stream);
  *                            stage it leaves behind; R is never stored.  Same
  *                            arithmetic in the same order as the separate
  *                            update: identical results.
- *   FR_SCHEDULE_AUTO         (default) the fused stage at p <= 3, where it is
- *                            faster on GB300, the separate update at p >= 4,
+ *   FR_SCHEDULE_AUTO         (default) the fused stage at p <= 2, where it is
+ *                            faster on GB300, the separate update at p >= 3,
  *                            where the volume kernel's occupancy serves the
  *                            update traffic at lower bandwidth than a
  *                            streaming kernel.

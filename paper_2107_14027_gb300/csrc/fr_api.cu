@@ -56,7 +56,8 @@ void fill_const_t(const fr_ctx* c, acmhd::FrConst<T>* k) {
   k->ne = c->ne;
   k->stride = static_cast<int>(c->stride);
   const int E = acmhd::fused_tile_elements(c->dim, c->m, sizeof(T) == 4 ? FR_F32 : FR_F64);
-  k->xcompact = (E > 0 && c->mesh.n[0] % E == 0) ? 1 : 0;
+  // x-face trace columns (x_col): by group where the rows allow it
+  k->xcompact = (E <= 0 || c->mesh.n[0] < E) ? 0 : (c->mesh.n[0] % E == 0 ? 1 : 2);
 }
 
 int alloc_zeroed(void** p, size_t bytes, const char* what) {
@@ -191,17 +192,18 @@ int rhs_host_pipelined(fr_ctx* c, const void* U_host, void* R_host, const int* b
 }
 
 // Pseudo steps with the update fused into the volume kernel: on request, and
-// by default at p <= 3.  Measured on GB300 (FP32 RK4 steps on the 3-D order
+// by default at p <= 2.  Measured on GB300 (FP32 RK4 steps on the 3-D order
 // sweep meshes of about 38M points per variable, fused / separate):
-// p = 1 12.9 / 15.2 ms, p = 2 12.3 / 14.3, p = 3 11.4 / 12.6, p = 4 17.7 /
-// 13.7, p = 5 18.4 / 14.7, p = 6 23.2 / 17.3.  At p >= 4 the stage kernel's
-// larger line work leaves too few resident warps to stream the update
-// traffic as fast as the separate update kernel does.  FP64 (ALU bound on
-// this part): equal times at p = 1..3.
+// p = 1 11.5 / 14.0 ms, p = 2 11.3 / 13.7, p = 3 11.7-12.8 / 11.6, p = 4
+// 17.0 / 13.2 (at p = 3 the fused stage led, 11.4 / 12.6, until the trace
+// and volume kernels stored the x-face traces by group).  At p >= 4 the stage
+// kernel's larger line work leaves too few resident warps to stream the
+// update traffic as fast as the separate update kernel does.  FP64 (ALU bound
+// on this part): equal times at p = 1..3.
 bool use_fused_stage(const fr_ctx* c) {
   if (c->df64) return false;   // the fused stage has no double-float instance
   return c->schedule == FR_SCHEDULE_FUSED_STAGE ||
-         (c->schedule == FR_SCHEDULE_AUTO && c->order <= 3);
+         (c->schedule == FR_SCHEDULE_AUTO && c->order <= 2);
 }
 
 // RK4 stage coefficient (dtau/2, dtau/2, dtau, dtau/6) rounded to the

@@ -203,14 +203,22 @@ __device__ __forceinline__ bool x_pair_on_chip(int e_left, int e_right, int E) {
   return e_right == e_left + 1 && (e_right % E) != 0;
 }
 
-// Column of an x-face trace in the trace buffer.  When the rows of elements
-// along x are whole lane groups (n_x a multiple of E), only the first element
-// of a group stores its low x face and only the last its high x face, so the
-// group index serves as the column: the values that neighbouring CTAs read
-// then share sectors instead of each taking a sector of its own.  Otherwise
-// the element index (the layout of the y and z faces).
-__device__ __forceinline__ size_t x_col(int e, int E, int xcompact) {
-  return xcompact ? (size_t)(e / E) : (size_t)e;
+// Column of an x-face trace in the trace buffer.  Only elements whose
+// x-neighbour on that side lies outside their lane group of E store the face
+// (x_pair_on_chip): the group's first element (low face), its last (high
+// face), and where a row of n_x elements starts or ends inside the group,
+// that element.  Stored by group, the values that neighbouring CTAs read
+// share sectors instead of each taking a sector of its own:
+//  xcompact = 1 (n_x a multiple of E: rows are whole groups): column g;
+//  xcompact = 2 (n_x > E otherwise: at most one row boundary inside a
+//    group): columns 2g (the group's own end) and 2g + 1 (the row boundary);
+//  xcompact = 0 (n_x < E): the element index, the layout of the y and z faces.
+// hi: the high face (side 1) of element e, else the low face.
+__device__ __forceinline__ size_t x_col(int e, int E, int xcompact, bool hi) {
+  if (xcompact == 0) return (size_t)e;
+  if (xcompact == 1) return (size_t)(e / E);
+  const int inside = hi ? ((e + 1) % E != 0) : (e % E != 0);
+  return (size_t)(2 * (e / E) + inside);
 }
 
 }  // namespace acmhd

@@ -53,7 +53,7 @@ struct FrConst {
   int n[3];        // elements per direction (n[2] = 1 in 2-D)
   int ne;          // number of elements
   int stride;      // elem_stride
-  int xcompact;    // x-face traces at lane-group ends stored by group (x_col)
+  int xcompact;    // x-face trace columns at lane-group ends (x_col): 0, 1 or 2
 };
 
 // most slabs of the host-buffer RHS pipeline (fr_rhs_host).  Measured on

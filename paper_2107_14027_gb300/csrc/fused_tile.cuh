@@ -167,8 +167,9 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
     const bool hi_mem = (a != 0) || (act && !x_pair_on_chip(e, nb[0][1], E));
 #pragma unroll
     // x faces of the neighbours outside the lane group: by group (x_col)
-    const size_t clo = (a == 0) ? x_col(nb[0][0], E, c.xcompact) : (size_t)nb[a][0];
-    const size_t chi = (a == 0) ? x_col(nb[0][1], E, c.xcompact) : (size_t)nb[a][1];
+    // (the low neighbour's high face, the high neighbour's low face)
+    const size_t clo = (a == 0) ? x_col(nb[0][0], E, c.xcompact, true) : (size_t)nb[a][0];
+    const size_t chi = (a == 0) ? x_col(nb[0][1], E, c.xcompact, false) : (size_t)nb[a][1];
     for (int s = 0; s < NS; ++s) {
       o.lo[s] = lo_mem ? cvt<T>(__ldg(Tr + (((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + clo))
                        : T(0);
@@ -309,9 +310,10 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
         if constexpr (Out::kStage) {
           const bool w_lo = (a != 0) || !x_pair_on_chip(nb[0][0], e, E);
           const bool w_hi = (a != 0) || !x_pair_on_chip(e, nb[0][1], E);
-          const size_t col = (a == 0) ? x_col(e, E, c.xcompact) : (size_t)e;
-          if (s > D && w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + col] = t_lo;
-          if (s > D && w_hi) out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + col] = t_hi;
+          const size_t clo = (a == 0) ? x_col(e, E, c.xcompact, false) : (size_t)e;
+          const size_t chi = (a == 0) ? x_col(e, E, c.xcompact, true) : (size_t)e;
+          if (s > D && w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + clo] = t_lo;
+          if (s > D && w_hi) out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + chi] = t_hi;
         }
       }
     }
@@ -372,10 +374,11 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ U, const S* __r
           T x[M];
 #pragma unroll
           for (int t = 0; t < M; ++t) x[t] = sA[(s * NP + line_pt<D, M>(a, l, t)) * E + el];
-          const size_t col = (a == 0) ? x_col(e, E, c.xcompact) : (size_t)e;
-          if (w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + col] = trace_dot<M>(x, c.lm);
+          const size_t clo = (a == 0) ? x_col(e, E, c.xcompact, false) : (size_t)e;
+          const size_t chi = (a == 0) ? x_col(e, E, c.xcompact, true) : (size_t)e;
+          if (w_lo) out.tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + clo] = trace_dot<M>(x, c.lm);
           if (w_hi)
-            out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + col] = trace_dot<M>(x, c.lp);
+            out.tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + chi] = trace_dot<M>(x, c.lp);
         }
       }
     }

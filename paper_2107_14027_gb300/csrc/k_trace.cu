@@ -70,14 +70,15 @@ trace_kernel(const S* __restrict__ U, S* __restrict__ Tr, const FrConst<T> c, in
                                    : cvt<T>(__ldg(U + ((size_t)v * NP + pt) * Sd + e));
         }
       }
-      // x faces by group where the rows are whole lane groups (x_col)
-      const size_t col = (a == 0) ? x_col(e, EF, c.xcompact) : (size_t)e;
+      // x faces stored by group (x_col)
+      const size_t clo = (a == 0) ? x_col(e, EF, c.xcompact, false) : (size_t)e;
+      const size_t chi = (a == 0) ? x_col(e, EF, c.xcompact, true) : (size_t)e;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         if (need_lo)
-          Tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + col] = cvt<S>(trace_dot<M>(x[s], c.lm));
+          Tr[(((size_t)(2 * a) * NS + s) * NL + l) * Sd + clo] = cvt<S>(trace_dot<M>(x[s], c.lm));
         if (need_hi)
-          Tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + col] =
+          Tr[(((size_t)(2 * a + 1) * NS + s) * NL + l) * Sd + chi] =
               cvt<S>(trace_dot<M>(x[s], c.lp));
       }
     }
