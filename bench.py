@@ -605,9 +605,9 @@ class _DualSolver:
                     continue
                 self.pm[j] = abi.fr_pmg_create(c, 1)
                 abi.fr_pmg_set_dtau(self.pm[j], factors, True)
-                if args.dual_pmg_bottom != 4 and order > 1:
+                if (args.dual_pmg_bottom != 4 or args.dual_pmg_post != 7) and order > 1:
                     sched = [(q, 1) for q in range(order, 1, -1)] + [(1, args.dual_pmg_bottom)]
-                    sched += [(q, 1) for q in range(2, order)] + [(order, 7)]
+                    sched += [(q, 1) for q in range(2, order)] + [(order, args.dual_pmg_post)]
                     abi.fr_pmg_set_cycle(self.pm[j], sched)
                 last = j == 1 or not self.refine
                 if args.dual_solver == "pmg-aa" and last:
@@ -657,7 +657,8 @@ def _dual_config(args, workload, extra):
            "anderson": args.dual_anderson if args.dual_solver == "pmg-aa" else 0,
            "fp64_twin": args.dual_twin,
            "pmg_factors": args.dual_pmg_factors or "1.75^(p-q)",
-           "pmg_bottom_iterations": args.dual_pmg_bottom}
+           "pmg_bottom_iterations": args.dual_pmg_bottom,
+           "pmg_finest_post_iterations": args.dual_pmg_post}
     cfg.update(extra)
     return cfg
 
@@ -1078,9 +1079,12 @@ def main():
     ap.add_argument("--dual-pmg-factors", default="",
                     help="pseudo-step multipliers for orders p, p-1, .., 1 (default 1.75^(p-q))")
     ap.add_argument("--dual-anderson", type=int, default=8, help="Anderson memory (pmg-aa)")
-    ap.add_argument("--dual-pmg-bottom", type=int, default=16,
+    ap.add_argument("--dual-pmg-post", type=int, default=1,
+                    help="RK4 iterations on the finest order on the way up a cycle (the "
+                         "paper's cycle: 7)")
+    ap.add_argument("--dual-pmg-bottom", type=int, default=32,
                     help="iterations on order 1 per cycle (the paper's cycle: 4; measured "
-                         "better: 16)")
+                         "better: 32 with one on the finest order going up)")
     ap.add_argument("--dual-pmg-iters-per-cycle", type=int, default=10,
                     help="fine-iteration equivalents of one cycle, to turn the iteration "
                          "caps into cycle caps")
