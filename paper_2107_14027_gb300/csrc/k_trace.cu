@@ -3,7 +3,8 @@
 //
 // Output layout: Tr[f][s][l][e], f = 2a + side (side 0: the face at -1 of
 // axis a, side 1: the face at +1), s the slot (fr_device.cuh), l the line
-// index along axis a, e the element (stride c.stride).
+// index along axis a, e the element (stride c.stride); the x faces (a = 0)
+// at the column x_col gives (by lane group where the rows allow it).
 //
 // Mapping: a warp covers E consecutive elements (lane -> element, so every
 // global access is one contiguous row) and 32/E lines at once; each thread
