@@ -782,8 +782,10 @@ def run_dual_steps(args):
     from paper_2107_14027_gb300 import abi
     from paper_2107_14027_gb300 import workloads as W
     n, order, lo, hi = _dual_case(args)
+    prec = abi.FR_F64 if args.dual_precision == 64 else abi.FR_F32
     U0 = W.taylor_green(n, lo, hi, order, dtype=np.float32)
-    S = _DualSolver(abi, args, abi.FR_F32, U0, n, lo, hi, order)
+    S = _DualSolver(abi, args, prec, U0 if prec == abi.FR_F32 else U0.astype(np.float64), n, lo,
+                    hi, order)
     abi.fr_dual_init(S.c, S.U)
     R = None
     if args.dual_fp64_ref > 0:
@@ -809,7 +811,7 @@ def run_dual_steps(args):
     out = {
         "metric": f"wall-s per physical step at {args.dual_tol:g} residual",
         "value": float(np.mean(walls)), "unit": "s", "higher_is_better": False, "n_gpus": 1,
-        "dtype": "f32+f64", "data": "synthetic",
+        "dtype": "f64" if prec == abi.FR_F64 else "f32+f64", "data": "synthetic",
         "config": _dual_config(args, f"hex_p{order}_{args.dual_mesh}cube_dual_steps",
                                {"steps": args.dual_steps, "fp64_reference_steps": args.dual_fp64_ref,
                                 "max_iter": args.dual_held_iters}),
