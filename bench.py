@@ -91,7 +91,7 @@ def _source_digest():
     """Digest of the fused RHS kernel's code (comments and blank lines
     dropped), to tell whether the committed ncu counters still describe it."""
     h = hashlib.sha256()
-    for name in ("k_fused.cu", "fused_tile.cuh", "fr_device.cuh"):
+    for name in ("k_fused.cu", "fused_tile.cuh", "fr_device.cuh", "xface_layout.h"):
         with open(os.path.join(ROOT, "paper_2107_14027_gb300", "csrc", name)) as f:
             for line in f:
                 code = line.split("//", 1)[0].rstrip()

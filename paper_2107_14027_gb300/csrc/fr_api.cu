@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "fr_internal.h"
+#include "xface_layout.h"
 
 namespace {
 
@@ -57,7 +58,7 @@ void fill_const_t(const fr_ctx* c, acmhd::FrConst<T>* k) {
   k->stride = static_cast<int>(c->stride);
   const int E = acmhd::fused_tile_elements(c->dim, c->m, sizeof(T) == 4 ? FR_F32 : FR_F64);
   // x-face trace columns (x_col): by group where the rows allow it
-  k->xcompact = (E <= 0 || c->mesh.n[0] < E) ? 0 : (c->mesh.n[0] % E == 0 ? 1 : 2);
+  k->xcompact = acmhd::x_compact_mode(c->mesh.n[0], E);
 }
 
 int alloc_zeroed(void** p, size_t bytes, const char* what) {
