@@ -12,7 +12,11 @@ Nothing here retypes the oracle's formulas.  The checks are:
     an axis permutation and under a periodic shift of the mesh;
   * the paper's printed sparsity of the ACM-HD flux (Sec. 3);
   * agreement of the sum-factorised path with the dense element-by-element
-    path that applies the FR divergence equation without the grouping.
+    path that applies the FR divergence equation without the grouping;
+  * the semi-discrete spectrum of the acoustic part (V = 0, nu = 0) with the
+    DG correction equals upwind DG's closed form, the roots of
+    R(-lambda h / c) = exp(+-i theta) with R the (p, p+1) Pade approximant
+    of exp, to 1e-9 of the largest eigenvalue (p = 1..5).
 """
 import json
 import os
@@ -352,3 +356,74 @@ def test_acm_eigenvalues_closed_form():
             c = np.sqrt(va * va + zeta)
             expect = np.sort([va - c] + [va] * (d - 1) + [va + c])
             np.testing.assert_allclose(lam, expect, rtol=0, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# semi-discrete acoustic spectrum against upwind DG's closed form
+# ---------------------------------------------------------------------------
+
+def _pade_sub_diagonal(p):
+    """Ascending coefficients of the numerator (degree p) and denominator
+    (degree p + 1) of the (p, p + 1) Pade approximant of exp(w)."""
+    from math import factorial as f
+    q = p + 1
+    num = [f(p + q - j) * f(p) / (f(p + q) * f(j) * f(p - j)) for j in range(p + 1)]
+    den = [(-1) ** j * f(p + q - j) * f(q) / (f(p + q) * f(j) * f(q - j)) for j in range(q + 1)]
+    return np.array(num + [0.0]), np.array(den)
+
+
+def _acoustic_spectrum_is_upwind_dg(p=2, N=5, zeta=2.5, L=3.0):
+    """With nu = 0 and the Jacobian taken at U = 0, the (P, u) rows of the RHS
+    for fields constant along y (a 2-D mesh of N x 1 elements) are 1-D linear
+    acoustics P_t + zeta u_x = 0, u_t + P_x = 0 (the gradient variables do not
+    feed back without viscosity, and the y faces see no jump).  There Rusanov
+    with s = sqrt(zeta) is the characteristic upwind flux (|A| = sqrt(zeta) I),
+    and FR with the DG correction is nodal DG (Huynh 2007), so the scheme is
+    upwind DG for the two characteristic families at speeds +-c, c = sqrt(zeta).
+    Upwind DG of degree p carries an element's inflow value g to its outflow
+    value R(-z) g, z = lambda h / c, R the (p, p+1) Pade approximant of exp
+    (Lesaint and Raviart 1974: DG in the marching variable).  On N periodic
+    elements a Bloch mode of phase theta therefore has R(-z) = exp(+-i theta).
+    The oracle's Jacobian comes from central differences at amplitude 1e-12,
+    at which the quadratic terms and the |V_n| part of the speed vanish
+    below rounding."""
+    from scipy.optimize import linear_sum_assignment
+    m = p + 1
+    mesh = fr.Mesh((N, 1), (0.0, 0.0), (L, 1.0))
+    prm = fr.Params(zeta, 0.0, 1.0)
+    n = 2 * m * N
+    Jm = np.zeros((n, n))
+    eps = 1e-12
+    col = 0
+    ok = True
+    for var in (0, 1):
+        for e in range(N):
+            for i in range(m):
+                X = np.zeros((acmhd.nvars(2), m * m, N))
+                X[var, i + m * np.arange(m), e] = 1.0
+                dR = (fr.rhs(eps * X, mesh, p, prm) - fr.rhs(-eps * X, mesh, p, prm)) / (2 * eps)
+                G = dR[:2].reshape(2, m, m, N)            # [var, j, i, e]
+                scale = np.abs(G).max()
+                ok &= bool(np.abs(G - G[:, :1]).max() <= 1e-9 * scale)   # constant along y
+                ok &= bool(np.abs(dR[2]).max() <= 1e-9 * scale)          # v stays zero
+                Jm[:, col] = G[:, 0].transpose(0, 2, 1).reshape(-1)      # (var, e, i)
+                col += 1
+    lam = np.linalg.eigvals(Jm)
+    num, den = _pade_sub_diagonal(p)
+    c, h = np.sqrt(zeta), L / N
+    expect = []
+    for k in range(N):
+        for sgn in (1.0, -1.0):
+            w = np.roots((num - np.exp(sgn * 2j * np.pi * k / N) * den)[::-1])
+            expect.extend(-w * c / h)
+    expect = np.array(expect)
+    if len(expect) != len(lam):
+        return False
+    cost = np.abs(lam[:, None] - expect[None, :])
+    r, cidx = linear_sum_assignment(cost)
+    return ok and bool(cost[r, cidx].max() <= 1e-9 * np.abs(expect).max())
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_acoustic_spectrum_is_upwind_dg(p):
+    assert _acoustic_spectrum_is_upwind_dg(p=p)

@@ -4,16 +4,19 @@ Each case plants one mistake in the oracle (on the CPU, by monkeypatching)
 and checks that at least one of the independent pins of
 tests/test_oracle_fr.py fails: convergence to the sympy continuous
 operators, discrete conservation, acoustic energy dissipation, agreement
-of the sum-factorised and dense paths, or the Rusanov speed against the
-spectral radius of the flux Jacobian.  (The manufactured-solution pin has
-its own planted mistake in tests/test_oracle_mms.py.)
+of the sum-factorised and dense paths, the Rusanov speed against the
+spectral radius of the flux Jacobian, or the acoustic Bloch spectrum
+against upwind DG's Pade closed form.  (The manufactured-solution pin has
+its own planted mistake in tests/test_oracle_mms.py.)  The spectrum pin is
+also checked alone on the mistakes it can see: those in the inviscid (P, V)
+part at V = 0.
 """
 import numpy as np
 import pytest
 
 from oracle import acmhd, fr, ops1d
-from tests.test_oracle_fr import (_continuous_case, _rand_state, _rusanov_speed_is_spectral_radius,
-                                  _sample, _weights)
+from tests.test_oracle_fr import (_acoustic_spectrum_is_upwind_dg, _continuous_case, _rand_state,
+                                  _rusanov_speed_is_spectral_radius, _sample, _weights)
 
 
 def _converges(d=2, p=2, ns=(8, 16), with_offset=True):
@@ -62,7 +65,7 @@ def _dense_agrees(d=2, p=2):
 
 def _all_pins_pass():
     return (_converges() and _conserves() and _dissipates() and _dense_agrees()
-            and _rusanov_speed_is_spectral_radius())
+            and _rusanov_speed_is_spectral_radius() and _acoustic_spectrum_is_upwind_dg())
 
 
 def test_unmutated_oracle_passes_all_pins():
@@ -180,3 +183,15 @@ def _source_sign(U, T):
 def test_planted_mistake_is_caught(name, monkeypatch):
     MUTATIONS[name](monkeypatch)
     assert not _all_pins_pass(), f"mutation {name} went undetected"
+
+
+# mistakes in the inviscid (P, V) part at V = 0, which the acoustic spectrum
+# sees without help (the reversed neighbour maps the Bloch spectrum onto itself)
+SPECTRUM_CATCHES = ["D_transposed", "anti_dissipative", "correction_sign", "corrections_swapped",
+                    "ends_swapped", "one_sided_flux", "speed_plus_zeta", "zeta_dropped"]
+
+
+@pytest.mark.parametrize("name", SPECTRUM_CATCHES)
+def test_acoustic_spectrum_pin_alone_catches(name, monkeypatch):
+    MUTATIONS[name](monkeypatch)
+    assert not _acoustic_spectrum_is_upwind_dg(), f"mutation {name} went undetected"
