@@ -31,8 +31,9 @@ periodic mesh, energy dissipation of the acoustic part, convergence to the
 continuous operators evaluated symbolically, axis-permutation symmetry, and
 agreement of the sum-factorised path with the dense Kronecker-product path
 (which applies the FR divergence equation directly, without the stage-3
-grouping), and the Bloch spectrum of the acoustic part with the DG
-correction against upwind DG's Pade closed form.  tests/test_oracle_mms.py: the steady solution of a manufactured
+grouping), the Bloch spectrum of the acoustic part with the DG
+correction against upwind DG's Pade closed form, and the exact energy
+balance of the operator linearised at V = 0.  tests/test_oracle_mms.py: the steady solution of a manufactured
 problem converges at order p + 1 in the velocity (at least p in the
 pressure, p in the gradient variables).
 """

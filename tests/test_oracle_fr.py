@@ -16,7 +16,11 @@ Nothing here retypes the oracle's formulas.  The checks are:
   * the semi-discrete spectrum of the acoustic part (V = 0, nu = 0) with the
     DG correction equals upwind DG's closed form, the roots of
     R(-lambda h / c) = exp(+-i theta) with R the (p, p+1) Pade approximant
-    of exp, to 1e-9 of the largest eigenvalue (p = 1..5).
+    of exp, to 1e-9 of the largest eigenvalue (p = 1..5);
+  * the exact energy balance of the operator linearised at V = 0 with the
+    DG correction and the gradient variables on: the weighted energy
+    1/2 sum W (P^2/zeta + |V|^2 + nu T |q|^2) changes at -nu sum W |q|^2
+    minus the Rusanov jump penalty, to 1e-10.
 """
 import json
 import os
@@ -427,3 +431,77 @@ def _acoustic_spectrum_is_upwind_dg(p=2, N=5, zeta=2.5, L=3.0):
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_acoustic_spectrum_is_upwind_dg(p):
     assert _acoustic_spectrum_is_upwind_dg(p=p)
+
+
+# ---------------------------------------------------------------------------
+# exact energy balance of the linearised operator
+# ---------------------------------------------------------------------------
+
+def _energy_balance(d, p, n, lengths, zeta=2.5, nu=0.3, T=0.2, seed=4, correction="dg"):
+    """(E', closed form) for the RHS linearised at U = 0 on random
+    discontinuous data with the gradient variables switched on.
+
+    At V = 0 the flux is linear, F_a = A_a U, and H = diag(1/zeta, I, nu T I)
+    makes every H A_a symmetric (the P-V_a pair couples by zeta and 1, the
+    V_i-q_ia pair by -nu and -1/T).  FR with the DG correction is DG with
+    exact Gauss-Legendre integration of these fluxes, so the energy
+    E = 1/2 sum W U.HU changes at exactly
+        E' = -nu sum W |q|^2 - (sqrt(zeta)/2) sum_faces sum w_f ([P]^2/zeta + |[V]|^2):
+    the volume terms integrate to face terms, the central parts of the
+    common flux cancel them, the Rusanov part (speed sqrt(zeta) at V = 0, on
+    P and V only) leaves the jump penalty, and the source -q/T gives the
+    first term.  Quadrature nodes, weights and end values come from numpy's
+    Gauss-Legendre rule here, not from the oracle."""
+    m = p + 1
+    mesh = fr.Mesh(n, (0.0,) * d, lengths)
+    prm = fr.Params(zeta, nu, T)
+    U = _rand_state(d, p, n, seed)
+    eps = 1e-12
+    R = (fr.rhs(eps * U, mesh, p, prm, correction)
+         - fr.rhs(-eps * U, mesh, p, prm, correction)) / (2 * eps)
+    xi, w = np.polynomial.legendre.leggauss(m)
+    ends = {}
+    for side in (-1.0, 1.0):
+        ends[side] = np.array([np.prod([(side - xi[j]) / (xi[k] - xi[j]) for j in range(m) if j != k])
+                               for k in range(m)])
+    nv = acmhd.nvars(d)
+    # A[v, point axes (slowest direction first), element axes (slowest first)]
+    A = U.reshape((nv,) + (m,) * d + tuple(reversed(n)))
+
+    def pax(a):
+        return 1 + (d - 1 - a)
+
+    def eax(a):
+        return 1 + d + (d - 1 - a)
+
+    Wpt = np.ones((m,) * d)
+    for a in range(d):
+        shape = [1] * d
+        shape[d - 1 - a] = m
+        Wpt = Wpt * (w * mesh.h[a] / 2).reshape(shape)
+    Wpt = Wpt.reshape(-1)                       # matches pt = i + m j + m^2 k
+    H = np.array([1.0 / zeta] + [1.0] * d + [nu * T] * (d * d))
+    lhs = float(np.einsum("v,p,vpe,vpe->", H, Wpt, U, R))
+    rhs = -nu * float(np.einsum("p,vpe->", Wpt, U[1 + d:] ** 2))
+    for a in range(d):
+        hi = np.tensordot(A, ends[1.0], axes=([pax(a)], [0]))
+        lo = np.tensordot(A, ends[-1.0], axes=([pax(a)], [0]))
+        # after contracting the point axis, element axis of a sits one lower
+        jump = np.roll(lo, -1, axis=eax(a) - 1) - hi       # right neighbour's low face - own high
+        wf = np.ones((m,) * (d - 1))
+        others = [b for b in range(d) if b != a]
+        for b in others:
+            shape = [1] * (d - 1)
+            shape[(d - 2) - others.index(b)] = m
+            wf = wf * (w * mesh.h[b] / 2).reshape(shape)
+        wf = wf.reshape(wf.shape + (1,) * d)
+        pen = jump[0] ** 2 / zeta + (jump[1:1 + d] ** 2).sum(0)
+        rhs -= 0.5 * np.sqrt(zeta) * float((wf * pen).sum())
+    return lhs, rhs
+
+
+@pytest.mark.parametrize("d,p,n", [(2, 1, (4, 3)), (2, 3, (3, 4)), (3, 2, (3, 2, 4)), (3, 4, (2, 3, 2))])
+def test_energy_balance_of_the_linearised_operator(d, p, n):
+    lhs, rhs = _energy_balance(d, p, n, (1.0, 1.7, 0.8)[:d])
+    assert rhs < 0
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)

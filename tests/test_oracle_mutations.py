@@ -5,18 +5,20 @@ and checks that at least one of the independent pins of
 tests/test_oracle_fr.py fails: convergence to the sympy continuous
 operators, discrete conservation, acoustic energy dissipation, agreement
 of the sum-factorised and dense paths, the Rusanov speed against the
-spectral radius of the flux Jacobian, or the acoustic Bloch spectrum
-against upwind DG's Pade closed form.  (The manufactured-solution pin has
-its own planted mistake in tests/test_oracle_mms.py.)  The spectrum pin is
-also checked alone on the mistakes it can see: those in the inviscid (P, V)
-part at V = 0.
+spectral radius of the flux Jacobian, the acoustic Bloch spectrum against
+upwind DG's Pade closed form, or the exact energy balance of the operator
+linearised at V = 0.  (The manufactured-solution pin has its own planted
+mistake in tests/test_oracle_mms.py.)  The last two are also checked alone
+on the mistakes they can see: the spectrum those in the inviscid (P, V)
+part at V = 0, the energy balance all but the two that change the Rusanov
+speed only where V is not zero.
 """
 import numpy as np
 import pytest
 
 from oracle import acmhd, fr, ops1d
-from tests.test_oracle_fr import (_acoustic_spectrum_is_upwind_dg, _continuous_case, _rand_state,
-                                  _rusanov_speed_is_spectral_radius, _sample, _weights)
+from tests.test_oracle_fr import (_acoustic_spectrum_is_upwind_dg, _continuous_case, _energy_balance,
+                                  _rand_state, _rusanov_speed_is_spectral_radius, _sample, _weights)
 
 
 def _converges(d=2, p=2, ns=(8, 16), with_offset=True):
@@ -63,9 +65,15 @@ def _dense_agrees(d=2, p=2):
     return bool(np.allclose(fr.rhs_dense(U, mesh, p, prm), R, rtol=0, atol=1e-12 * np.abs(R).max()))
 
 
+def _energy_balance_holds():
+    lhs, rhs = _energy_balance(2, 2, (3, 4), (1.0, 1.7))
+    return bool(abs(lhs - rhs) <= 1e-10 * abs(rhs))
+
+
 def _all_pins_pass():
     return (_converges() and _conserves() and _dissipates() and _dense_agrees()
-            and _rusanov_speed_is_spectral_radius() and _acoustic_spectrum_is_upwind_dg())
+            and _rusanov_speed_is_spectral_radius() and _acoustic_spectrum_is_upwind_dg()
+            and _energy_balance_holds())
 
 
 def test_unmutated_oracle_passes_all_pins():
@@ -195,3 +203,13 @@ SPECTRUM_CATCHES = ["D_transposed", "anti_dissipative", "correction_sign", "corr
 def test_acoustic_spectrum_pin_alone_catches(name, monkeypatch):
     MUTATIONS[name](monkeypatch)
     assert not _acoustic_spectrum_is_upwind_dg(), f"mutation {name} went undetected"
+
+
+# every mistake but the two whose Rusanov speed differs only where V != 0
+ENERGY_CATCHES = sorted(set(MUTATIONS) - {"speed_sqrt_zeta", "speed_min_of_sides"})
+
+
+@pytest.mark.parametrize("name", ENERGY_CATCHES)
+def test_energy_balance_pin_alone_catches(name, monkeypatch):
+    MUTATIONS[name](monkeypatch)
+    assert not _energy_balance_holds(), f"mutation {name} went undetected"
